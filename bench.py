@@ -1,0 +1,377 @@
+"""Benchmark of the octagon-filter convex hull on GB300.
+
+Workload (one step): the device hull (extremes -> filter -> sort -> chain)
+of three synthetic sets of n = 10^8 binary32 points -- Normal(0,1),
+unit circle, displaced circle (radius 1 - |Normal(0, 0.01)|) -- i.e. the
+single-set workload at 10^8 points for the three study cases of the paper
+(Sec. 5).  Inputs (2.4 GB) are larger than L2 and resident in HBM before
+the timed region.
+
+Printed: one JSON line (rank 0).  ``value`` is points through the whole
+path per second, over all ranks.  ``e2e`` repeats the measurement through
+the public API with the inputs copied from pinned host memory and the hull
+copied back inside the timed region.  ``roofline`` is for the kernel with
+the largest share of device time (event-timed launches inside the timed
+region).  ``cpu_baseline`` times the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle as the reference arm on host
+cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s filtered (HBM GB/s vs peak); end-to-end hull ms, learned vs octagon"
+WORKLOAD = "hull of 3 single sets, n=1e8 fp32 each: normal(0,1), unit circle, displaced circle (r=1-|N(0,0.01)|)"
+N_POINTS = 100_000_000
+DISTS = ("normal", "circle", "displaced")
+KERNEL_IDS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- inputs
+
+def make_inputs(n, seed):
+    import pointgen
+    return [pointgen.make_points(d, n, seed=seed + k) for k, d in enumerate(DISTS)]
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline bookkeeping
+
+def algorithmic_bytes(kernel, n, s_list):
+    """Bytes a kernel must move per launch (summed over the step's launches),
+    from the data it reads and writes by definition."""
+    if kernel == "extremes":
+        return sum(8 * n for _ in s_list)
+    if kernel == "filter":
+        return sum(8 * n + 12 * s for s in s_list)
+    if kernel == "sort_hist":
+        return sum(8 * s for s in s_list)
+    if kernel == "sort_pass":
+        return sum(24 * s for s in s_list)   # per executed pass: read key+val, write key+val
+    return None
+
+
+def load_traffic(kernel):
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel
+    source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel)
+        if not rec:
+            return None
+        src = os.path.join(ROOT, "paper_2303_10581_gb300", "csrc", rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != rec.get("source_sha"):
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- CPU oracle timing
+
+def cpu_oracle_rate(sample_n, seed):
+    import oracle
+    pts = make_inputs(sample_n, seed + 100)
+    t0 = time.perf_counter()
+    for p in pts:
+        oracle.convex_hull(p)
+    dt = time.perf_counter() - t0
+    return len(pts) * sample_n / dt / 1e9, dt
+
+
+# --------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    sample_n = 1_000_000
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sample_n // 10, args.seed)
+    times = []
+    for _ in range(args.steps):
+        rate, dt = cpu_oracle_rate(sample_n, args.seed)
+        times.append(dt)
+    pts_per_step = 3 * sample_n
+    value = pts_per_step * len(times) / sum(times) / 1e9
+    sample = f"{sample_n} points of each of the 3 distributions per step (full workload: {args.n} each)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+exact",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gpoints/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2303_10581_gb300 as ch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    host = make_inputs(n, args.seed)
+    d_pts = [torch.from_numpy(p).to(dev) for p in host]
+    ws = ch.Workspace(n, device=dev)
+    hull_idx = [torch.empty(n, dtype=torch.int32, device=dev) for _ in DISTS]
+    hull_cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in DISTS]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k in range(len(DISTS)):
+            ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up, then one probed step for the kernel shares and survivor counts
+    for _ in range(args.warmup):
+        step()
+    ws.check()
+    ch.ch_probe_start(KERNEL_IDS, max_launches=64)
+    step()
+    probe_all = ch.ch_probe_stop()
+    ws.check()
+    dominant = max(probe_all, key=lambda k: probe_all[k][0])
+    total_probe = sum(v[0] for v in probe_all.values())
+    shares = {k: round(v[0] / total_probe, 4) for k, v in probe_all.items() if v[1]}
+    hull_sizes = [int(c.item()) for c in hull_cnt]
+    # survivor counts: ask the filter directly (same polygon, same result)
+    surv = []
+    for k in range(len(DISTS)):
+        e = ch.extremes(d_pts[k], ws)
+        _, _, cnt = ch.filter_points(d_pts[k], e, ws, with_points=False)
+        surv.append(int(cnt.item()))
+    ws.check()
+
+    # timed region: the dominant kernel's launches are event-timed on the stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ch.ch_probe_start([dominant], max_launches=64 * args.steps)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    barrier()
+    probe = ch.ch_probe_stop()
+    clk = clocks.stop()
+    ws.check()
+    ms = t0.elapsed_time(t1) / args.steps
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    pts_per_step = len(DISTS) * n
+    value = world * pts_per_step / (ms_max * 1e-3) / 1e9
+    launches_per_step = sum(v[1] for v in probe.values()) / args.steps
+
+    # roofline of the dominant kernel
+    dom_ms, dom_launches = probe[dominant]
+    peak, peak_kind = peaks()
+    roof = None
+    if dom_launches:
+        per_step_bytes = algorithmic_bytes(dominant, n, surv)
+        if per_step_bytes is not None:
+            launches_step = dom_launches / args.steps
+            if dominant == "sort_pass":
+                executed = [0 if s <= 1 else 1 for s in surv]
+                per_launch_bytes = per_step_bytes / max(1, launches_step)
+            else:
+                per_launch_bytes = per_step_bytes / max(1, launches_step)
+            avg_ms = dom_ms / dom_launches
+            achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+            tr = load_traffic(dominant)
+            roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                    "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4)}
+
+    # filter-only throughput (the paper's headline stage) from its own launches
+    filt = None
+    if probe_all["filter"][1]:
+        fms = probe_all["filter"][0]
+        fb = algorithmic_bytes("filter", n, surv)
+        filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / 3, 4),
+                "gbs": round(fb / (fms * 1e-3) / 1e9, 1), "frac_of_peak": round(fb / (fms * 1e-3) / 1e9 / peak, 4)}
+
+    # end to end through the public API: pinned host -> device, hull, device -> host
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(p).pin_memory() for p in host]
+        out_host = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in DISTS]
+        cnt_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in DISTS]
+
+        def e2e_step():
+            d2h = 0
+            for k in range(len(DISTS)):
+                d_pts[k].copy_(pinned[k], non_blocking=True)
+                ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+                cnt_host[k].copy_(hull_cnt[k], non_blocking=True)
+            stream.synchronize()
+            for k in range(len(DISTS)):
+                h = int(cnt_host[k].item())
+                out_host[k][:h].copy_(hull_idx[k][:h], non_blocking=True)
+                d2h += 4 + 4 * h
+            stream.synchronize()
+            return d2h
+
+        e2e_step()
+        barrier()
+        w0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            d2h = e2e_step()
+        barrier()
+        e_ms = (time.perf_counter() - w0) * 1e3 / args.steps
+        t = torch.tensor([e_ms], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+        e2e = {"value": round(world * pts_per_step / (e_ms * 1e-3) / 1e9, 3), "unit": "Gpoints/s",
+               "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": 8 * n * len(DISTS),
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample_n = 1_000_000
+        rate, dt = cpu_oracle_rate(sample_n, args.seed)
+        cpu = {"value": round(rate, 5), "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sample_n} points of each distribution (3 sets), whole path, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+exact", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_per_set": n, "sets_per_step": len(DISTS),
+                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
+                       "survivors": dict(zip(DISTS, surv)), "hull_sizes": dict(zip(DISTS, hull_sizes))},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roof, "filter": filt, "kernel_shares": shares, "clocks": clk, "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

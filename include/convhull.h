@@ -1,0 +1,142 @@
+/*
+ * convhull.h -- C ABI of the GB300 octagon-filter convex-hull library.
+ *
+ * Method: Carrasco, Ferrada, Navarro, Hitschfeld, "An Evaluation of GPU
+ * Filters for Accelerating the 2D Convex Hull" (arXiv 2303.10581),
+ * Algorithm 1: findingPolygon -> buildingFilter ->
+ * compactingFilteredPoints -> convexHull_algorithm.  Every step runs in
+ * hand-written sm_103a CUDA kernels; nothing here falls back to the host.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Points are packed binary32 pairs (x, y), x at the lower address:
+ *    `pts` holds 2*n floats.  Coordinates must be finite.  8-byte alignment
+ *    is required, 16-byte alignment is preferred (vector loads).
+ *  - Every array argument is a DEVICE pointer owned by the caller; the
+ *    library allocates nothing.  `ws` is caller-owned device scratch of at
+ *    least ch_workspace_size() bytes, 256-byte aligned; it must be zeroed
+ *    once (ch_workspace_init) before its first use and then belongs to the
+ *    library until the calls that use it have completed.  One workspace
+ *    serves one stream at a time.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream: outputs, including
+ *    counts, are written to device memory and are valid once the stream
+ *    reaches the call.
+ *  - Argument errors are detected on the host and returned at once; no work
+ *    is enqueued then.  Errors found on the device (non-finite input, a
+ *    look-back wait that timed out) are recorded in `ws` and reported by
+ *    ch_last_error(); outputs of a failed call are unspecified.
+ *  - Point indices are uint32: n < 2^32 (ch_hull: n < 2^30).
+ *  - Orientation signs are exact (binary32 fast test with a proven error
+ *    bound, then binary64, then error-free expansion arithmetic).
+ */
+#ifndef CONVHULL_H
+#define CONVHULL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CH_OK = 0,
+    CH_ERR_ARG = 1,         /* bad pointer, size or alignment               */
+    CH_ERR_NONFINITE = 2,   /* a coordinate is NaN or infinite              */
+    CH_ERR_CAPACITY = 3,    /* workspace too small / n beyond the limit     */
+    CH_ERR_CUDA = 4,        /* a CUDA runtime call failed                   */
+    CH_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+    CH_ERR_UNSUPPORTED = 6  /* device is not sm_103 or feature unavailable  */
+} ch_status;
+
+/* Bytes of workspace needed for point sets of up to n points in total,
+ * split into up to num_sets sets (num_sets = 1 for the single-set calls).
+ * No CUDA work.  Returns CH_ERR_ARG for negative sizes or a NULL `bytes`. */
+ch_status ch_workspace_size(int64_t n, int64_t num_sets, size_t *bytes);
+
+/* Zero a workspace of ws_bytes bytes on `stream` (one cudaMemsetAsync).
+ * Needed once before first use, and again after a call reported an error. */
+ch_status ch_workspace_init(void *ws, size_t ws_bytes, void *stream);
+
+/* Sec. 3.1 (findingPolygon): the eight polygon vertices.
+ * ext8[0..7] receives point indices in counter-clockwise order
+ *   R = argmax x, TR = argmax fl(x+y), T = argmax y, TL = argmin fl(x-y),
+ *   L = argmin x, BL = argmin fl(x+y), B = argmin y, BR = argmax fl(x-y),
+ * the corner points being the points closest in Manhattan distance to the
+ * bounding-box corners.  fl() is binary32 round-to-nearest.  Ties go to the
+ * lowest index; -0 and +0 compare equal.  n >= 1.  A NaN or infinite
+ * coordinate sets CH_ERR_NONFINITE in ws (ext8 is then unspecified). */
+ch_status ch_extremes(const float *pts, int64_t n, uint32_t *ext8,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Sec. 3.2 (buildingFilter + compactingFilteredPoints): discard the points
+ * lying strictly inside the closed polygon pts[ext8[0]], ..., pts[ext8[7]]
+ * (strictly left of every edge of non-zero length), keep all others, and
+ * compact the kept ones stably.  surv_idx (capacity n) receives the kept
+ * indices in ascending order, surv_pts (capacity 2n floats, may be NULL)
+ * their coordinates, and *surv_count (device) their number.  ext8 is a
+ * device array, normally the output of ch_extremes.  n == 0 writes a zero
+ * count. */
+ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8,
+                    uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Algorithm 1 end to end on the device: extremes, filter, then Andrew's
+ * monotone chain over the survivors (Sec. 3.3; the paper hands this step to
+ * a CPU library, here it stays on the GPU).  hull_idx (capacity n)
+ * receives original point indices counter-clockwise, starting at the
+ * lexicographically smallest (x, y) vertex; equal points count once (the
+ * lowest index is reported); points on a hull edge are not vertices.
+ * *hull_count (device) receives the vertex count: 0 for n == 0, 1 when all
+ * points coincide, 2 when all are collinear. */
+ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Many independent sets in one call.  Set b is pts[offsets[b] .. offsets[b+1])
+ * (offsets is a DEVICE array of num_sets+1 non-decreasing int64, offsets[0]
+ * = 0).  Set b's hull is written, as set-local indices in the same order as
+ * ch_hull, to hull_idx[hull_offsets[b] ..], with hull_offsets (device,
+ * num_sets+1 entries) the exclusive prefix sum of the hull sizes.
+ * hull_idx capacity: offsets[num_sets] entries.  ws must be sized with
+ * ch_workspace_size(offsets[num_sets], num_sets).  Not part of the paper:
+ * the batched form of the same path. */
+ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_sets,
+                          uint32_t *hull_idx, int64_t *hull_offsets,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* Waits for `stream`, then returns and clears the first device-side error
+ * recorded in ws since the last call (CH_OK if none). */
+ch_status ch_last_error(void *ws, void *stream);
+
+/* ---- instrumentation (not part of the paper's method) ------------------
+ * Kernel identifiers of the path, in launch order. */
+typedef enum {
+    CH_K_EXTREMES = 0,   /* Sec. 3.1 sweep (+ polygon build in its last block) */
+    CH_K_OCTAGON = 1,    /* polygon build for ch_filter                        */
+    CH_K_FILTER = 2,     /* Sec. 3.2 fused test + stable compaction            */
+    CH_K_SORT_HIST = 3,  /* digit histograms of the survivor keys              */
+    CH_K_SORT_PASS = 4,  /* one radix-sort pass                                 */
+    CH_K_CHAIN = 5,      /* Sec. 3.3 chunk chains + tree merges                 */
+    CH_K_EMIT = 6,       /* compaction of the chain ranges                      */
+    CH_K_FINISH = 7,     /* hull assembly                                       */
+    CH_K_COUNT = 8
+} ch_kernel_id;
+
+/* Start timing: every later launch of a kernel whose bit (1 << id) is set in
+ * kernel_mask is bracketed by two CUDA events recorded on its launch stream,
+ * for at most max_launches launches per kernel.  Launch counting for all
+ * kernels restarts at zero.  Host-only bookkeeping; creates the events. */
+ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
+
+/* Stop timing: waits for the recorded events, writes per kernel id the summed
+ * event-measured milliseconds (ms[CH_K_COUNT], 0 when not timed) and the
+ * number of launches since ch_probe_start (launches[CH_K_COUNT]), and
+ * releases the events.  Either pointer may be NULL. */
+ch_status ch_probe_stop(double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONVHULL_H */

@@ -1,0 +1,113 @@
+// api.cu -- the extern "C" entry points declared in include/convhull.h.
+// Host code only: argument checks, workspace layout, launches.  No
+// allocation, no host synchronisation (except ch_last_error), no host
+// fallback: every step of Algorithm 1 runs in the kernels of this library.
+#include <cstring>
+
+#include "common.cuh"
+#include "launch.h"
+
+using namespace ch;
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline ch_status check_ws(void *ws, size_t ws_bytes, const Layout &L)
+{
+    if (!ws || !aligned(ws, 256)) return CH_ERR_ARG;
+    if (ws_bytes < L.total) return CH_ERR_CAPACITY;
+    return CH_OK;
+}
+
+inline ch_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CH_OK : CH_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" ch_status ch_workspace_size(int64_t n, int64_t num_sets, size_t *bytes)
+{
+    if (!bytes || n < 0 || num_sets < 1) return CH_ERR_ARG;
+    if (n > kMaxN) return CH_ERR_CAPACITY;
+    *bytes = make_layout(n).total;
+    return CH_OK;
+}
+
+extern "C" ch_status ch_workspace_init(void *ws, size_t ws_bytes, void *stream)
+{
+    if (!ws || !aligned(ws, 256) || ws_bytes < sizeof(Persist)) return CH_ERR_ARG;
+    return cuda_status(cudaMemsetAsync(ws, 0, ws_bytes, as_stream(stream)));
+}
+
+extern "C" ch_status ch_extremes(const float *pts, int64_t n, uint32_t *ext8, void *ws, size_t ws_bytes,
+                                 void *stream)
+{
+    if (!pts || !ext8 || n < 1 || !aligned(pts, 8) || !aligned(ext8, 4)) return CH_ERR_ARG;
+    if (n > kMaxN) return CH_ERR_CAPACITY;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    return cuda_status(launch_extremes(pts, n, ws, L, ext8, false, nullptr, 0, as_stream(stream)));
+}
+
+extern "C" ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8, uint32_t *surv_idx,
+                               float *surv_pts, uint32_t *surv_count, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!surv_count || n < 0 || !aligned(surv_count, 4)) return CH_ERR_ARG;
+    if (n > kMaxN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(surv_count, 0, sizeof(uint32_t), st));
+    if (!pts || !ext8 || !surv_idx || !aligned(pts, 8) || !aligned(ext8, 4) || !aligned(surv_idx, 4) ||
+        (surv_pts && !aligned(surv_pts, 8)))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    cudaError_t e = launch_octagon(pts, n, ext8, ws, L, at<unsigned long long>(ws, L.ctrl),
+                                   (int64_t)L.zero_words, st);
+    if (e != cudaSuccess) return CH_ERR_CUDA;
+    return cuda_status(launch_filter(pts, n, ws, L, surv_idx, surv_pts, surv_count, false, st));
+}
+
+extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
+                             size_t ws_bytes, void *stream)
+{
+    if (!hull_count || n < 0 || !aligned(hull_count, 4)) return CH_ERR_ARG;
+    if (n >= kMaxHullN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(hull_count, 0, sizeof(uint32_t), st));
+    if (!pts || !hull_idx || !aligned(pts, 8) || !aligned(hull_idx, 4)) return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
+                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st);
+    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st);
+    if (e == cudaSuccess) e = launch_sort(ws, L, st);
+    if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
+    return cuda_status(e);
+}
+
+extern "C" ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_sets, uint32_t *hull_idx,
+                                     int64_t *hull_offsets, void *ws, size_t ws_bytes, void *stream)
+{
+    (void)pts;
+    (void)offsets;
+    (void)num_sets;
+    (void)hull_idx;
+    (void)hull_offsets;
+    (void)ws;
+    (void)ws_bytes;
+    (void)stream;
+    return CH_ERR_UNSUPPORTED;
+}
+
+extern "C" ch_status ch_last_error(void *ws, void *stream)
+{
+    if (!ws || !aligned(ws, 256)) return CH_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CH_ERR_CUDA;
+    Persist *p = at<Persist>(ws, 0);
+    uint32_t code = 0;
+    if (cudaMemcpy(&code, &p->error, sizeof code, cudaMemcpyDeviceToHost) != cudaSuccess) return CH_ERR_CUDA;
+    if (code != 0 && cudaMemset(p, 0, 2 * sizeof(uint32_t)) != cudaSuccess) return CH_ERR_CUDA;
+    return static_cast<ch_status>(code);
+}

@@ -1,0 +1,376 @@
+// common.cuh -- shared device definitions of the octagon-filter hull path:
+// workspace layout, order-preserving float keys, the exact orientation
+// predicate and the bounded-wait helpers.
+//
+// Method: Carrasco et al., "An Evaluation of GPU Filters for Accelerating
+// the 2D Convex Hull", Sec. 3 / Algorithm 1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/convhull.h"
+
+namespace ch {
+
+// ---------------------------------------------------------------------------
+// launch geometry
+// ---------------------------------------------------------------------------
+constexpr int kExtThreads = 512;      // extremes sweep
+constexpr int kFiltThreads = 256;     // fused test + compaction
+constexpr int kFiltItems = 16;        // points per thread per tile
+constexpr int kFiltTile = kFiltThreads * kFiltItems;   // 4096 points = 32 KB
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys
+constexpr int kSortPasses = 8;        // 64-bit keys, 8-bit digits
+constexpr int kChainC = 64;           // points per leaf chunk of the chain
+constexpr int kChainThreads = 128;
+constexpr int kEmitThreads = 256;     // chunks per emit tile (one per thread)
+constexpr int64_t kMaxHullN = (int64_t)1 << 30;
+constexpr int64_t kMaxN = ((int64_t)1 << 32) - 1;
+
+// device error codes mirror ch_status
+constexpr uint32_t kErrNonFinite = CH_ERR_NONFINITE;
+constexpr uint32_t kErrTimeout = CH_ERR_TIMEOUT;
+// bounded waits: polls before a look-back wait is declared dead (each poll
+// is followed by a short nanosleep once the first few fail)
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// look-back status words: [flag:2 | value:62]
+constexpr uint64_t kFlagA = 1ull << 62;   // tile aggregate published
+constexpr uint64_t kFlagP = 2ull << 62;   // inclusive prefix published
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+// 32-bit variant for the radix-sort digit status: [flag:2 | value:30]
+constexpr uint32_t kFlagA32 = 1u << 30;
+constexpr uint32_t kFlagP32 = 2u << 30;
+constexpr uint32_t kVal32 = (1u << 30) - 1;
+
+// ---------------------------------------------------------------------------
+// filter polygon (Sec. 3.1 -> Sec. 3.2)
+// ---------------------------------------------------------------------------
+struct Octagon {
+    // edge k runs from vertex k to vertex k+1 (mod 8), vertices in the
+    // order R, TR, T, TL, L, BL, B, BR
+    float ax[8], ay[8];     // edge start
+    float bx[8], by[8];     // edge end
+    float dx[8], dy[8];     // fl(b - a)
+    float bound[8];         // static error bound of the binary32 test (+inf: off)
+    uint32_t valid;         // bit k: edge k has non-zero length
+    uint32_t has_edges;     // at least one valid edge
+    uint32_t abort;         // non-finite input: later stages do nothing
+    uint32_t pad;
+    float xl, xh, yl, yh;   // closed quick-discard rectangle (xl > xh: none)
+    float cx, cy;           // bounding-box centre, for the edge order
+};
+
+// extremes reduction state: left zeroed by the last block of every sweep
+struct ExtCtrl {
+    unsigned long long ext_slot[8];   // packed (key, index) per extreme
+    uint32_t ext_done;                // extremes blocks finished
+    uint32_t nonfinite;               // a non-finite coordinate was seen
+};
+
+// control block: zeroed at the start of every call (together with the
+// filter's look-back status, which follows it)
+struct Ctrl {
+    uint32_t filt_ticket;             // tile tickets of the fused filter
+    uint32_t surv_count;              // survivors
+    uint32_t sort_ticket[kSortPasses];
+    uint32_t hist[kSortPasses][256];  // digit histograms of the survivor keys
+    uint32_t pass_src[kSortPasses];   // 0/1: buffer a pass reads
+    uint32_t pass_skip[kSortPasses];  // pass is an identity (one digit only)
+    uint32_t final_buf;               // buffer holding the sorted keys
+    uint32_t hist_done;
+    uint32_t emit_ticket[2];
+    uint32_t h_lower, h_upper;
+    uint32_t pad[2];
+};
+
+// persistent words: survive calls, cleared by ch_last_error
+struct Persist {
+    uint32_t error;
+    uint32_t error_site;
+    uint32_t pad[62];
+};
+
+// Workspace layout for a problem of up to n points.
+struct Layout {
+    size_t persist, extctrl, oct, ext8;
+    size_t ctrl;            // Ctrl, immediately followed by
+    size_t filt_status;     // u64[filt_tiles]
+    size_t zero_words;      // u64 words from ctrl to the end of filt_status
+    size_t keys[2];         // u64[n]
+    size_t vals[2];         // u32[n]
+    size_t sort_status[2];  // u32[sort_tiles * 256]
+    size_t chainL, chainU;  // u32[n_chunks * C]
+    size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
+    size_t node;            // int32[5 * n_nodes]: firstL lastL firstU lastU counter
+    size_t emit_status[2];  // u64[emit_tiles]
+    size_t utmp;            // u32[n]
+    size_t total;
+    int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__host__ __device__ inline int64_t tree_nodes(int64_t nc)
+{
+    // nodes of all levels >= 1 of the binary merge tree over nc leaves
+    int64_t total = 0, w = nc;
+    while (w > 1) {
+        w = (w + 1) / 2;
+        total += w;
+    }
+    return total;
+}
+
+__host__ __device__ inline Layout make_layout(int64_t n)
+{
+    Layout L{};
+    if (n < 1) n = 1;
+    L.n = n;
+    L.filt_tiles = ceil_div(n, kFiltTile);
+    L.sort_tiles = ceil_div(n, kSortTile);
+    L.n_chunks = ceil_div(n, kChainC);
+    L.n_nodes = tree_nodes(L.n_chunks) + 1;
+    L.emit_tiles = ceil_div(L.n_chunks, kEmitThreads);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.persist = take(sizeof(Persist));
+    L.extctrl = take(sizeof(ExtCtrl));
+    L.oct = take(sizeof(Octagon));
+    L.ext8 = take(8 * sizeof(uint32_t));
+    L.ctrl = take(sizeof(Ctrl));
+    L.filt_status = take((size_t)L.filt_tiles * 8);
+    L.zero_words = (L.filt_status + (size_t)L.filt_tiles * 8 - L.ctrl + 7) / 8;
+    L.keys[0] = take((size_t)n * 8);
+    L.keys[1] = take((size_t)n * 8);
+    L.vals[0] = take((size_t)n * 4);
+    L.vals[1] = take((size_t)n * 4);
+    L.sort_status[0] = take((size_t)L.sort_tiles * 256 * 4);
+    L.sort_status[1] = take((size_t)L.sort_tiles * 256 * 4);
+    L.chainL = take((size_t)L.n_chunks * kChainC * 4);
+    L.chainU = take((size_t)L.n_chunks * kChainC * 4);
+    L.chunk = take((size_t)L.n_chunks * 8 * 4);
+    L.node = take((size_t)L.n_nodes * 5 * 4);
+    L.emit_status[0] = take((size_t)L.emit_tiles * 8);
+    L.emit_status[1] = take((size_t)L.emit_tiles * 8);
+    L.utmp = take((size_t)n * 4);
+    L.total = o;
+    return L;
+}
+
+template <class T>
+__host__ __device__ inline T *at(void *ws, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+// ---------------------------------------------------------------------------
+// order-preserving keys
+// ---------------------------------------------------------------------------
+// Map binary32 bits to uint32 so that unsigned order equals numeric order;
+// -0 is first mapped to +0 so the two compare equal, as float compares do.
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    if (b == 0x80000000u) b = 0;
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_float(uint32_t k)
+{
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+__device__ __forceinline__ unsigned long long point_key(float x, float y)
+{
+    return ((unsigned long long)ord_key(x) << 32) | ord_key(y);
+}
+
+__device__ __forceinline__ float2 key_point(unsigned long long k)
+{
+    return make_float2(key_float((uint32_t)(k >> 32)), key_float((uint32_t)k));
+}
+
+// ---------------------------------------------------------------------------
+// exact orientation: sign of (b - a) x (c - a) for binary32 inputs
+// ---------------------------------------------------------------------------
+// Tier 3: the determinant expands into six products of two binary32 values
+// (the a.x*a.y terms cancel); each is exact in binary64.  They are summed
+// without error by Grow-Expansion with Two-Sum (Shewchuk, "Adaptive
+// Precision Floating-Point Arithmetic and Fast Robust Geometric
+// Predicates", 1997, Sec. 2); the sign of a non-overlapping expansion is
+// the sign of its largest non-zero component.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+
+static __device__ __noinline__ int orient_exact(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    double t[6];
+    t[0] = __dmul_rn((double)bx, (double)cy);
+    t[1] = -__dmul_rn((double)bx, (double)ay);
+    t[2] = -__dmul_rn((double)ax, (double)cy);
+    t[3] = -__dmul_rn((double)by, (double)cx);
+    t[4] = __dmul_rn((double)by, (double)ax);
+    t[5] = __dmul_rn((double)ay, (double)cx);
+    double e[6];
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double q = t[i];
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            if (j < m) {
+                double s, r;
+                two_sum(q, e[j], s, r);
+                q = s;
+                if (r != 0.0) e[k++] = r;
+            }
+        }
+        if (q != 0.0) e[k++] = q;
+        m = k;
+    }
+    if (m == 0) return 0;
+    return e[m - 1] > 0.0 ? 1 : -1;
+}
+
+// Tier 2: binary64 evaluation with Shewchuk's orient2d error bound
+// ccwerrboundA = (3 + 16 eps) eps, eps = 2^-53.  Differences and products of
+// binary32 values cannot underflow or overflow in binary64, so the bound
+// holds; undecided cases go to tier 3.
+static __device__ __noinline__ int orient_d(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    // orient2d(pa = a, pb = b, pc = c)
+    double detleft = __dmul_rn(__dsub_rn((double)ax, (double)cx), __dsub_rn((double)by, (double)cy));
+    double detright = __dmul_rn(__dsub_rn((double)ay, (double)cy), __dsub_rn((double)bx, (double)cx));
+    double det = __dsub_rn(detleft, detright);
+    double detsum;
+    if (detleft > 0.0) {
+        if (detright <= 0.0) return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+        detsum = __dadd_rn(detleft, detright);
+    } else if (detleft < 0.0) {
+        if (detright >= 0.0) return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+        detsum = __dsub_rn(-detleft, detright);
+    } else {
+        return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+    }
+    const double errA = (3.0 + 16.0 * 0x1p-53) * 0x1p-53;   // exact in binary64
+    double eb = __dmul_ru(errA, detsum);
+    if (det >= eb) return 1;
+    if (-det >= eb) return -1;
+    return orient_exact(ax, ay, bx, by, cx, cy);
+}
+
+// Tier 1: binary32 evaluation with a dynamic bound.  The expression has
+// Shewchuk's orient2d shape (four differences, two products, one
+// subtraction), whose rounding error is below (3 + 16 eps) eps * detsum with
+// eps = 2^-24 when nothing under- or overflows; 4 eps * detsum leaves room
+// for the rounding of the bound itself, and 2^-140 absorbs the absolute
+// error of products that fall into the subnormal range.  Non-finite or
+// undecided cases go to tier 2.
+__device__ __forceinline__ int orient(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    float detleft = __fmul_rn(__fsub_rn(ax, cx), __fsub_rn(by, cy));
+    float detright = __fmul_rn(__fsub_rn(ay, cy), __fsub_rn(bx, cx));
+    float det = __fsub_rn(detleft, detright);
+    float detsum = __fadd_rn(fabsf(detleft), fabsf(detright));
+    float eb = __fmaf_ru(detsum, 2.384185791015625e-07f /* 2^-22 */, 7.174648137343064e-43f /* 2^-140 */);
+    if (detsum <= 3.0e38f) {
+        if (det > eb) return 1;
+        if (-det > eb) return -1;
+    }
+    return orient_d(ax, ay, bx, by, cx, cy);
+}
+
+// ---------------------------------------------------------------------------
+// error reporting and bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_error(void *ws, const Layout &L, uint32_t code, uint32_t site)
+{
+    Persist *p = at<Persist>(ws, L.persist);
+    if (atomicCAS(&p->error, 0u, code) == 0u) atomicExch(&p->error_site, site);
+}
+
+__device__ __forceinline__ bool error_set(void *ws, const Layout &L)
+{
+    return *(volatile uint32_t *)&at<Persist>(ws, L.persist)->error != 0u;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", 2016) over 64-bit status words, run by one
+// full warp.  Returns the exclusive prefix of tile `tile`.  Waits are
+// bounded: when a predecessor never publishes, the error word is set and
+// the wait stops (the prefix is then meaningless, the call reports
+// CH_ERR_TIMEOUT).
+__device__ __forceinline__ unsigned long long lookback_u64(unsigned long long *status, int64_t tile,
+                                                           void *ws, const Layout &L, uint32_t site)
+{
+    const uint32_t lane = lane_id();
+    unsigned long long excl = 0;
+    int64_t base = tile - 1;
+    uint32_t spins = 0;
+    while (base >= 0) {
+        int64_t idx = base - (int64_t)lane;
+        unsigned long long s = idx >= 0 ? ld_acquire_u64(status + idx) : kFlagP;
+        while (__any_sync(0xffffffffu, (s >> 62) == 0)) {
+            if (++spins > kSpinLimit || (spins > 1024 && error_set(ws, L))) {
+                if (lane == 0) set_error(ws, L, kErrTimeout, site);
+                return 0;
+            }
+            if (spins > 64) __nanosleep(100);
+            if ((s >> 62) == 0) s = ld_acquire_u64(status + idx);
+        }
+        uint32_t pmask = __ballot_sync(0xffffffffu, (s >> 62) == 2);
+        uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 31u;
+        unsigned long long v = lane <= stop ? (s & kValMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pmask) break;
+        base -= 32;
+    }
+    return excl;
+}
+
+}  // namespace ch

@@ -1,0 +1,36 @@
+// launch.h -- host-side launchers shared between the translation units of
+// the library (internal; the public interface is include/convhull.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ch {
+
+int sm_count();
+
+// instrumentation around every launch (probe.cu)
+void probe_before(int kid, cudaStream_t st);
+void probe_after(int kid, cudaStream_t st);
+
+cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
+                            bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
+                            cudaStream_t st);
+
+cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, void *ws, const Layout &L,
+                           unsigned long long *zero_ptr, int64_t zero_words, cudaStream_t st);
+
+// fused point test + stable compaction.  keys_mode: write (point key, index)
+// pairs into the sort buffers of ws instead of (index, point) outputs.
+cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
+                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st);
+
+// stable LSD radix sort of the survivor (key, index) pairs held in ws
+cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);
+
+// monotone chain over the sorted survivors; writes the hull
+cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st);
+
+}  // namespace ch

@@ -1,0 +1,55 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every entry point declared in include/*.h; host argument checks
+return their documented status without touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2303_10581_gb300 as ch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\bch_status\s+(ch_\w+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_entry_points():
+    assert declared_symbols() == set(ch.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ch.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_workspace_size_is_monotone_and_host_only():
+    sizes = [ch.ch_workspace_size(n) for n in (0, 1, 4096, 4097, 10**6, 10**8)]
+    assert all(a <= b for a, b in zip(sizes, sizes[1:]))
+    assert sizes[-1] > 24 * 10**8   # sort buffers dominate
+
+
+def test_host_argument_errors():
+    lib = ch.load()
+    out = ctypes.c_size_t(0)
+    assert lib.ch_workspace_size(-1, 1, ctypes.byref(out)) == ch.CH_ERR_ARG
+    assert lib.ch_workspace_size(10, 0, ctypes.byref(out)) == ch.CH_ERR_ARG
+    assert lib.ch_workspace_size(1 << 33, 1, ctypes.byref(out)) == ch.CH_ERR_CAPACITY
+    assert lib.ch_extremes(None, 10, None, None, 0, None) == ch.CH_ERR_ARG
+    assert lib.ch_extremes(8, 0, 16, 256, 1 << 20, None) == ch.CH_ERR_ARG          # n < 1
+    assert lib.ch_extremes(4, 10, 16, 256, 1 << 20, None) == ch.CH_ERR_ARG         # pts misaligned
+    assert lib.ch_extremes(8, 10, 16, 256, 16, None) == ch.CH_ERR_CAPACITY         # ws too small
+    assert lib.ch_extremes(8, 10, 16, 100, 1 << 20, None) == ch.CH_ERR_ARG         # ws misaligned
+    assert lib.ch_filter(8, 10, 16, 32, None, None, 256, 1 << 20, None) == ch.CH_ERR_ARG   # no count
+    assert lib.ch_hull(8, 1 << 30, 16, 32, 256, 1 << 40, None) == ch.CH_ERR_CAPACITY
+    assert lib.ch_hull(8, 10, 16, None, 256, 1 << 20, None) == ch.CH_ERR_ARG
+    assert lib.ch_last_error(None, None) == ch.CH_ERR_ARG
