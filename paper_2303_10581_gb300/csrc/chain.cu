@@ -37,7 +37,8 @@ struct ChainPtrs {
     const uint32_t *vals;
     uint32_t *chain[2];      // lower, upper
     int32_t *lo[2], *hi[2], *prv[2], *nxt[2];
-    int32_t *node;           // 5 ints per node: firstL lastL firstU lastU counter
+    int32_t *node;           // 4 ints per node: firstL lastL firstU lastU
+    int32_t *node_cnt;       // arrivals per node (zeroed at the start of each call)
 };
 
 __device__ __forceinline__ ChainPtrs chain_ptrs(void *ws, const Layout &L, uint32_t buf)
@@ -58,6 +59,7 @@ __device__ __forceinline__ ChainPtrs chain_ptrs(void *ws, const Layout &L, uint3
     P.prv[1] = ck + 6 * nc;
     P.nxt[1] = ck + 7 * nc;
     P.node = at<int32_t>(ws, L.node);
+    P.node_cnt = at<int32_t>(ws, L.node_cnt);
     return P;
 }
 
@@ -85,8 +87,8 @@ __device__ __forceinline__ void node_ends(const ChainPtrs &P, int level, int64_t
         const bool live = ldcg(P.hi[side] + j) >= ldcg(P.lo[side] + j);
         first = last = live ? (int32_t)j : -1;
     } else {
-        first = ldcg(P.node + (nb + j) * 5 + 2 * side);
-        last = ldcg(P.node + (nb + j) * 5 + 2 * side + 1);
+        first = ldcg(P.node + (nb + j) * 4 + 2 * side);
+        last = ldcg(P.node + (nb + j) * 4 + 2 * side + 1);
     }
 }
 
@@ -211,9 +213,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(void *ws, Layout L
                 for (int side = 0; side < 2; ++side) node_ends(P, level, nb_child, node, side, rec[2 * side], rec[2 * side + 1]);
             } else {
                 __threadfence();
-                int32_t *cnt = P.node + (nb + parent) * 5 + 4;
-                if (atomicAdd(cnt, 1) == 0) break;   // first to arrive: the sibling merges
-                *cnt = 0;                           // last user of the counter: reset
+                if (atomicAdd(P.node_cnt + nb + parent, 1) == 0) break;   // first to arrive: the sibling merges
                 __threadfence();
                 const int64_t a = parent * 2, b = a + 1;
 #pragma unroll
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(void *ws, Layout L
                 }
             }
 #pragma unroll
-            for (int f = 0; f < 4; ++f) P.node[(nb + parent) * 5 + f] = rec[f];
+            for (int f = 0; f < 4; ++f) P.node[(nb + parent) * 4 + f] = rec[f];
             node = parent;
             nb_child = nb;
             nb += pw;

@@ -98,14 +98,15 @@ struct Persist {
 struct Layout {
     size_t persist, extctrl, oct, ext8;
     size_t ctrl;            // Ctrl, immediately followed by
-    size_t filt_status;     // u64[filt_tiles]
-    size_t zero_words;      // u64 words from ctrl to the end of filt_status
+    size_t filt_status;     // u64[filt_tiles] and
+    size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node
+    size_t zero_words;      // u64 words from ctrl to the end of node_cnt
     size_t keys[2];         // u64[n]
     size_t vals[2];         // u32[n]
     size_t sort_status[2];  // u32[sort_tiles * 256]
     size_t chainL, chainU;  // u32[n_chunks * C]
     size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
-    size_t node;            // int32[5 * n_nodes]: firstL lastL firstU lastU counter
+    size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
     size_t emit_status[2];  // u64[emit_tiles]
     size_t utmp;            // u32[n]
     size_t total;
@@ -149,7 +150,8 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     L.ext8 = take(8 * sizeof(uint32_t));
     L.ctrl = take(sizeof(Ctrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
-    L.zero_words = (L.filt_status + (size_t)L.filt_tiles * 8 - L.ctrl + 7) / 8;
+    L.node_cnt = take((size_t)L.n_nodes * 4);
+    L.zero_words = (L.node_cnt + (size_t)L.n_nodes * 4 - L.ctrl + 7) / 8;
     L.keys[0] = take((size_t)n * 8);
     L.keys[1] = take((size_t)n * 8);
     L.vals[0] = take((size_t)n * 4);
@@ -159,7 +161,7 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     L.chainL = take((size_t)L.n_chunks * kChainC * 4);
     L.chainU = take((size_t)L.n_chunks * kChainC * 4);
     L.chunk = take((size_t)L.n_chunks * 8 * 4);
-    L.node = take((size_t)L.n_nodes * 5 * 4);
+    L.node = take((size_t)L.n_nodes * 4 * 4);
     L.emit_status[0] = take((size_t)L.emit_tiles * 8);
     L.emit_status[1] = take((size_t)L.emit_tiles * 8);
     L.utmp = take((size_t)n * 4);
