@@ -109,6 +109,24 @@ ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_
  * recorded in ws since the last call (CH_OK if none). */
 ch_status ch_last_error(void *ws, void *stream);
 
+/* ch_filter for callers that cannot allocate device memory and cannot pass
+ * a workspace -- e.g. code inside a host framework that owns every device
+ * allocation, or a path under a fixed memory budget or a latency budget
+ * that cudaMalloc's implicit synchronisation would break.  The paper has no
+ * counterpart; this is a packaging of the same filter.
+ * Same arguments, results and error codes as ch_filter, without ws: the
+ * scratch lives in a 160 KiB static device array inside the library, held
+ * by every GPU that loads it until the process exits.  n is limited to
+ * 2^26 = 67,108,864 points (CH_ERR_CAPACITY beyond).  Allocates nothing.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU race and
+ * must be serialised by the caller.  Device-side errors cannot be queried
+ * (a bad ext8 index yields a zero count). */
+ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32_t *ext8,
+                            uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
+                            void *stream);
+
 /* ---- instrumentation (not part of the paper's method) ------------------
  * Kernel identifiers of the path, in launch order. */
 typedef enum {

@@ -31,7 +31,7 @@ STATUS = {
 CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOUT, CH_ERR_UNSUPPORTED = range(7)
 
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
-           "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop")
+           "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish")
 
 
@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
     lib.ch_last_error.argtypes = [p, p]
     lib.ch_probe_start.argtypes = [ctypes.c_uint32, ctypes.c_int32]
     lib.ch_probe_stop.argtypes = [p, p]
+    lib.ch_filter_noalloc.argtypes = [p, i64, p, p, p, p, p]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -120,6 +121,15 @@ def ch_filter(pts, ext8, surv_idx, surv_pts, surv_count, ws, stream=None):
     _check(load().ch_filter(_ptr(pts, "pts"), pts.shape[0], _ptr(ext8, "ext8"), _ptr(surv_idx, "surv_idx"),
                             _ptr(surv_pts, "surv_pts"), _ptr(surv_count, "surv_count"), _ptr(ws, "ws"),
                             ws.numel(), _stream(stream)), "ch_filter")
+
+
+def ch_filter_noalloc(pts, ext8, surv_idx, surv_pts, surv_count, stream=None):
+    """ch_filter without a workspace, for callers that cannot allocate device
+    memory (the library's own static scratch is used; n <= 2^26; calls that
+    overlap on the GPU race)."""
+    _check(load().ch_filter_noalloc(_ptr(pts, "pts"), pts.shape[0], _ptr(ext8, "ext8"),
+                                    _ptr(surv_idx, "surv_idx"), _ptr(surv_pts, "surv_pts"),
+                                    _ptr(surv_count, "surv_count"), _stream(stream)), "ch_filter_noalloc")
 
 
 def ch_hull(pts, hull_idx, hull_count, ws, stream=None):
