@@ -35,7 +35,8 @@ if ROOT not in sys.path:
 METRIC = "Gpoints/s filtered (HBM GB/s vs peak); end-to-end hull ms, learned vs octagon"
 WORKLOAD = "hull of 3 single sets, n=1e8 fp32 each: normal(0,1), unit circle, displaced circle (r=1-|N(0,0.01)|)"
 N_POINTS = 100_000_000
-DISTS = ("normal", "circle", "displaced")
+ALL_DISTS = ("normal", "circle", "displaced")
+DISTS = ALL_DISTS
 KERNEL_IDS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish")
 
 
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dists", default=",".join(ALL_DISTS),
+                    help="subset of the workload's distributions (profiling runs)")
     return ap.parse_args()
 
 
@@ -63,7 +66,7 @@ def dist_env():
 
 def make_inputs(n, seed):
     import pointgen
-    return [pointgen.make_points(d, n, seed=seed + k) for k, d in enumerate(DISTS)]
+    return [pointgen.make_points(d, n, seed=seed + ALL_DISTS.index(d)) for d in DISTS]
 
 
 # --------------------------------------------------------------------------- clocks
@@ -120,16 +123,21 @@ class ClockSampler:
 # --------------------------------------------------------------------------- roofline bookkeeping
 
 def algorithmic_bytes(kernel, n, s_list):
-    """Bytes a kernel must move per launch (summed over the step's launches),
-    from the data it reads and writes by definition."""
+    """Bytes a kernel must move in one step (all its launches for the step's
+    sets), from the data it reads and writes by definition; s_list holds the
+    survivor count of each set."""
     if kernel == "extremes":
-        return sum(8 * n for _ in s_list)
+        return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
-        return sum(8 * n + 12 * s for s in s_list)
+        return sum(8 * n + 12 * s for s in s_list)          # read points, write key + index per survivor
     if kernel == "sort_hist":
-        return sum(8 * s for s in s_list)
+        return sum(4 * s for s in s_list)                   # read the 32-bit keys
     if kernel == "sort_pass":
-        return sum(24 * s for s in s_list)   # per executed pass: read key+val, write key+val
+        # 4 passes (32-bit x key) per set with more than one survivor; each
+        # reads and writes key (4 B) + payload (8 B): 24 B per survivor
+        return sum(4 * 24 * s for s in s_list if s > 1)
+    if kernel == "chain":
+        return sum(12 * s for s in s_list)                  # read the sorted keys and payloads once
     return None
 
 
@@ -234,9 +242,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     ws.check()
-    ch.ch_probe_start(KERNEL_IDS, max_launches=64)
-    step()
-    probe_all = ch.ch_probe_stop()
+    # one probed step, set by set: event time of every kernel
+    per_set = {}
+    probe_all = {k: (0.0, 0) for k in KERNEL_IDS}
+    for k in range(len(DISTS)):
+        ch.ch_probe_start(KERNEL_IDS, max_launches=64)
+        ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+        pr = ch.ch_probe_stop()
+        per_set[DISTS[k]] = {kk: round(v[0], 4) for kk, v in pr.items() if v[1]}
+        probe_all = {kk: (probe_all[kk][0] + pr[kk][0], probe_all[kk][1] + pr[kk][1]) for kk in KERNEL_IDS}
     ws.check()
     dominant = max(probe_all, key=lambda k: probe_all[k][0])
     total_probe = sum(v[0] for v in probe_all.values())
@@ -282,14 +296,11 @@ def run_ours(args):
     if dom_launches:
         per_step_bytes = algorithmic_bytes(dominant, n, surv)
         if per_step_bytes is not None:
-            launches_step = dom_launches / args.steps
-            if dominant == "sort_pass":
-                executed = [0 if s <= 1 else 1 for s in surv]
-                per_launch_bytes = per_step_bytes / max(1, launches_step)
-            else:
-                per_launch_bytes = per_step_bytes / max(1, launches_step)
+            # algorithmic bytes of all timed launches over their summed event
+            # time (= per-launch bytes over the average launch duration)
+            per_launch_bytes = per_step_bytes * args.steps / dom_launches
             avg_ms = dom_ms / dom_launches
-            achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+            achieved = per_step_bytes * args.steps / (dom_ms * 1e-3) / 1e9
             tr = load_traffic(dominant)
             roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
@@ -301,7 +312,7 @@ def run_ours(args):
     if probe_all["filter"][1]:
         fms = probe_all["filter"][0]
         fb = algorithmic_bytes("filter", n, surv)
-        filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / 3, 4),
+        filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / len(DISTS), 4),
                 "gbs": round(fb / (fms * 1e-3) / 1e9, 1), "frac_of_peak": round(fb / (fms * 1e-3) / 1e9 / peak, 4)}
 
     # end to end through the public API: pinned host -> device, hull, device -> host
@@ -357,7 +368,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
                        "survivors": dict(zip(DISTS, surv)), "hull_sizes": dict(zip(DISTS, hull_sizes))},
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "roofline": roof, "filter": filt, "kernel_shares": shares, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "filter": filt, "kernel_shares": shares, "kernel_ms_per_set": per_set,
+            "hull_ms_per_set": {d: round(sum(v.values()), 4) for d, v in per_set.items()},
+            "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -366,7 +379,10 @@ def run_ours(args):
 
 
 def main():
+    global DISTS
     args = parse()
+    DISTS = tuple(d for d in args.dists.split(",") if d)
+    assert DISTS and all(d in ALL_DISTS for d in DISTS), args.dists
     if args.impl == "reference":
         run_reference(args)
     else:

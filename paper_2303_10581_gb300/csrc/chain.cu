@@ -1,25 +1,47 @@
 // chain.cu -- Sec. 3.3 of Carrasco et al. (convexHull_algorithm), kept on
-// the device: Andrew's monotone chain over the sorted survivors.
+// the device: Andrew's monotone chain over the survivors sorted by x.
 //
 // The paper copies the candidates to the host and calls CGAL; its
 // conclusion names a fully device-resident hull as the next step.  Here:
 //
-//  1. leaf chains: the sorted survivors are cut into chunks of kChainC
-//     points; one thread runs the sequential monotone chain (lower and
-//     upper) over its chunk, skipping repeats of the previous point.
-//  2. merges: chunk chains are merged pairwise up a binary tree.  The
-//     second child to finish merges the pair (no thread ever waits).  Two
-//     x-ordered lower chains A | B merge by walking the common tangent:
-//     the cursor b on B moves right while B's next vertex is on or below
+//  0. runs: the survivors arrive sorted by x (equal x in ascending index
+//     order).  In a run of equal x only the lowest point can be a vertex of
+//     the lower chain and only the highest one of the upper chain, because
+//     the others lie strictly above (below) it on the same vertical.  The
+//     exceptions are the first x, whose lowest point starts both chains and
+//     whose highest point follows it on the upper chain, and the last x,
+//     whose highest point ends both chains after its lowest point on the
+//     lower chain.  Each run is reduced to those representatives (first
+//     occurrence on ties, i.e. the lowest index, which also collapses equal
+//     points).  A block owns the runs starting in its 4096-point
+//     super-chunk and looks ahead (block-parallel) when its last run
+//     continues past the super-chunk.
+//  1. elimination: per side, parallel passes over the representatives drop
+//     every point whose turn with its current neighbours is not strict (for
+//     the lower chain: on or above the segment joining them).  Such a point
+//     lies on or above a segment between two points of the set, so it is
+//     not a strict vertex of the lower hull and the sequential chain would
+//     pop it too; a sequence where every turn is strict is its own monotone
+//     chain.  Passes repeat until nothing changes or kElimPasses is
+//     reached; each is a compaction with a block scan.  On dense circles
+//     the first pass alone removes 70-99% of the points.
+//  2. leaf chains and merges: what is left is cut into leaves of 16; one
+//     thread runs the sequential monotone chain on each.  Chains are merged
+//     pairwise up a binary tree -- first inside the block over its 256
+//     leaves (shared memory, one level per barrier), then across
+//     super-chunks in global memory by a second kernel, where the second
+//     child to finish merges the pair (no thread ever waits).  Two
+//     x-ordered lower chains A | B merge by walking the common tangent: the
+//     cursor b on B moves right while B's next vertex is on or below
 //     line(a, b); the cursor a on A moves left while A's previous vertex is
-//     on or below line(a, b); repeat until neither moves.  The merged
-//     chain is A up to a followed by B from b, which is what the sequential
-//     chain produces (same pops, same collinear exclusion).  Each chunk
-//     keeps the surviving range [lo, hi] of its chain, and chunks whose
-//     range empties are unlinked from a list of live chunks.  Upper chains
-//     are handled the same way with the predicate mirrored.
+//     on or below line(a, b); repeat until neither moves.  The merged chain
+//     is A up to a followed by B from b, which is what the sequential chain
+//     produces (same pops, same collinear exclusion).  Each chunk keeps the
+//     surviving range [lo, hi] of its chain; chunks whose range empties are
+//     unlinked from a list of live chunks.  Upper chains are handled the
+//     same way with the predicate mirrored.
 //  3. emit: one pass compacts the live ranges (decoupled look-back over
-//     chunk counts) into the lower chain and the upper chain, and the
+//     super-chunk counts) into the lower chain and the upper chain, and the
 //     final kernel appends the upper chain, reversed and without its end
 //     points, behind the lower one: counter-clockwise from the
 //     lexicographically smallest point.
@@ -30,24 +52,213 @@ namespace ch {
 
 namespace {
 
-constexpr int C = kChainC;
+constexpr int LC = kLeafC;          // points per leaf
+constexpr int LT = kChainThreads;   // leaves per super-chunk
+constexpr int SC = kChainC;         // points per super-chunk
+constexpr int CS = kChainStride;    // chain slots per super-chunk
+constexpr int NL = SC + 2;          // sequence capacity: SC points + 2 look-ahead slots
 
+// pop / advance test: lower chains drop a vertex when the turn is not
+// strictly counter-clockwise, upper chains when it is not strictly clockwise
+__device__ __forceinline__ bool drop(int side, const float2 &a, const float2 &b, const float2 &c)
+{
+    const int o = orient(a.x, a.y, b.x, b.y, c.x, c.y);
+    return side == 0 ? o <= 0 : o >= 0;
+}
+
+// ---------------------------------------------------------------------------
+// tangent walk, shared by the in-block and the global merge
+// ---------------------------------------------------------------------------
+// Acc provides lo/hi/prv/nxt get+set per chunk and point(side, chunk, k).
+template <class Acc>
+__device__ void merge_walk(Acc &A, int side, int fa, int la, int fb, int lb)
+{
+    int ca = la, ka = A.hi(side, ca);
+    int cb = fb, kb = A.lo(side, cb);
+    int loa = A.lo(side, ca), hib = A.hi(side, cb);
+    float2 pa = A.point(side, ca, ka);
+    float2 pb = A.point(side, cb, kb);
+    for (;;) {
+        bool moved = false;
+        for (;;) {   // advance b
+            int nc = cb, nk = kb + 1, nhi = hib;
+            if (kb >= hib) {
+                if (cb == lb) break;
+                nc = A.nxt(side, cb);
+                nk = A.lo(side, nc);
+                nhi = A.hi(side, nc);
+            }
+            const float2 q = A.point(side, nc, nk);
+            if (!drop(side, pa, pb, q)) break;
+            if (nc != cb) {   // chunk cb is now entirely removed
+                A.set_range(side, cb, 1, 0);
+                cb = nc;
+                hib = nhi;
+            }
+            kb = nk;
+            pb = q;
+            moved = true;
+        }
+        for (;;) {   // retreat a
+            int pc = ca, pk = ka - 1, plo = loa;
+            if (ka <= loa) {
+                if (ca == fa) break;
+                pc = A.prv(side, ca);
+                plo = A.lo(side, pc);
+                pk = A.hi(side, pc);
+            }
+            const float2 q = A.point(side, pc, pk);
+            if (!drop(side, q, pa, pb)) break;
+            if (pc != ca) {
+                A.set_range(side, ca, 1, 0);
+                ca = pc;
+                loa = plo;
+            }
+            ka = pk;
+            pa = q;
+            moved = true;
+        }
+        if (!moved) break;
+    }
+    A.set_hi(side, ca, ka);
+    A.set_lo(side, cb, kb);
+    A.link(side, ca, cb);
+}
+
+// ---------------------------------------------------------------------------
+// in-block state; one side (lower or upper) is processed at a time
+// ---------------------------------------------------------------------------
+struct ChainSmem {
+    float2 pts[NL];               // staged points; [SC], [SC+1]: look-ahead lowest / highest
+    uint16_t list[3][NL];         // run starts, sequences and elimination ping-pong
+    uint8_t stk[LC * LT];         // leaf stacks: entry j of leaf t at [j * LT + t]
+    int16_t lo[LT], hi[LT], prv[LT], nxt[LT], first[LT], last[LT];
+    uint32_t wsum[LT / 32];
+    uint32_t total;
+    float red_y[2][LT / 32];      // look-ahead reduction scratch
+    uint32_t red_q[2][LT / 32];
+    uint32_t ext_pos[2];          // global positions of the look-ahead lowest / highest
+    float prev_x;
+    int has_prev;
+    int seq_len;
+};
+
+// leaf c covers sequence positions [c * LC, c * LC + LC); its stack holds
+// offsets into that range
+struct SmemAcc {
+    ChainSmem &s;
+    const uint16_t *lst;
+    __device__ int lo(int, int c) const { return s.lo[c]; }
+    __device__ int hi(int, int c) const { return s.hi[c]; }
+    __device__ int prv(int, int c) const { return s.prv[c]; }
+    __device__ int nxt(int, int c) const { return s.nxt[c]; }
+    __device__ void set_range(int, int c, int l, int h) const
+    {
+        s.lo[c] = (int16_t)l;
+        s.hi[c] = (int16_t)h;
+    }
+    __device__ void set_lo(int, int c, int l) const { s.lo[c] = (int16_t)l; }
+    __device__ void set_hi(int, int c, int h) const { s.hi[c] = (int16_t)h; }
+    __device__ void link(int, int a, int b) const
+    {
+        s.nxt[a] = (int16_t)b;
+        s.prv[b] = (int16_t)a;
+    }
+    __device__ float2 point(int, int c, int k) const { return s.pts[lst[c * LC + s.stk[k * LT + c]]]; }
+};
+
+// Exclusive scan of one count per thread over the block; the total goes to
+// s.total.  Contains two barriers.
+__device__ __forceinline__ uint32_t block_scan(ChainSmem &s, uint32_t v)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s.wsum[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < LT / 32; ++w) {
+        const uint32_t u = s.wsum[w];
+        if (w < warp) before += u;
+        total += u;
+    }
+    if (t == 0) s.total = total;
+    __syncthreads();
+    return before + incl - v;
+}
+
+// Stable compaction of positions [0, count).  Warp w owns the segment
+// [w*S, w*S + S) and walks it 32 consecutive positions at a time, so lanes
+// touch consecutive entries (no bank conflicts); keep(j) decides, out
+// receives src(j) for the kept j.  Returns the number kept (all threads).
+template <class Keep, class Src>
+__device__ __forceinline__ int block_compact(ChainSmem &s, int count, Keep keep, Src src, uint16_t *out)
+{
+    constexpr int NWARP = LT / 32;
+    constexpr int MAXC = (NL + NWARP * 32 - 1) / (NWARP * 32) + 1;   // 32-position chunks per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int S = (((count + NWARP - 1) / NWARP) + 31) & ~31;   // segment, a multiple of 32
+    const int j0 = warp * S;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t masks[MAXC];
+    int n = 0;
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+        uint32_t m = 0;
+        if (c * 32 < S) {
+            const int j = j0 + c * 32 + lane;
+            m = __ballot_sync(0xffffffffu, j < count && keep(j));
+        }
+        masks[c] = m;
+        n += __popc(m);
+    }
+    if (lane == 0) s.wsum[warp] = (uint32_t)n;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+        const uint32_t u = s.wsum[w];
+        if (w < warp) before += u;
+        total += u;
+    }
+    uint32_t o = before;
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+        const uint32_t m = masks[c];
+        if ((m >> lane) & 1u) out[o + __popc(m & lt)] = src(j0 + c * 32 + lane);
+        o += __popc(m);
+    }
+    __syncthreads();
+    return (int)total;
+}
+
+// ---------------------------------------------------------------------------
+// global state (one "chunk" = one super-chunk)
+// ---------------------------------------------------------------------------
 struct ChainPtrs {
-    const unsigned long long *keys;
-    const uint32_t *vals;
-    uint32_t *chain[2];      // lower, upper
+    const uint32_t *keys;             // sorted ord(x)
+    const unsigned long long *pay;    // sorted ord(y) << 32 | index
+    uint32_t *pos[2];                 // chain vertices: sorted positions, super-chunk c at [c * CS, ...)
+    float2 *pt[2];                    // chain vertices: coordinates
     int32_t *lo[2], *hi[2], *prv[2], *nxt[2];
-    int32_t *node;           // 4 ints per node: firstL lastL firstU lastU
-    int32_t *node_cnt;       // arrivals per node (zeroed at the start of each call)
+    int32_t *node;                    // 4 ints per tree node: firstL lastL firstU lastU
+    int32_t *node_cnt;                // arrivals per node (zeroed at the start of each call)
 };
 
 __device__ __forceinline__ ChainPtrs chain_ptrs(void *ws, const Layout &L, uint32_t buf)
 {
     ChainPtrs P;
-    P.keys = at<unsigned long long>(ws, L.keys[buf]);
-    P.vals = at<uint32_t>(ws, L.vals[buf]);
-    P.chain[0] = at<uint32_t>(ws, L.chainL);
-    P.chain[1] = at<uint32_t>(ws, L.chainU);
+    P.keys = at<uint32_t>(ws, L.keys[buf]);
+    P.pay = at<unsigned long long>(ws, L.pay[buf]);
+    for (int side = 0; side < 2; ++side) {
+        P.pos[side] = at<uint32_t>(ws, L.chain_pos[side]);
+        P.pt[side] = at<float2>(ws, L.chain_pt[side]);
+    }
     int32_t *ck = at<int32_t>(ws, L.chunk);
     const int64_t nc = L.n_chunks;
     P.lo[0] = ck + 0 * nc;
@@ -63,190 +274,358 @@ __device__ __forceinline__ ChainPtrs chain_ptrs(void *ws, const Layout &L, uint3
     return P;
 }
 
-__device__ __forceinline__ int32_t ldcg(const int32_t *p) { return __ldcg(p); }
-
-__device__ __forceinline__ float2 vertex(const ChainPtrs &P, int side, int32_t c, int32_t k)
+__device__ __forceinline__ float2 sorted_point(const ChainPtrs &P, int64_t q)
 {
-    const uint32_t pos = __ldcg(P.chain[side] + (int64_t)c * C + k);
-    return key_point(__ldg(P.keys + pos));
+    return make_float2(key_float(__ldg(P.keys + q)), key_float((uint32_t)(__ldg(P.pay + q) >> 32)));
 }
 
-// pop / advance test: lower chains drop a vertex when the turn is not
-// strictly counter-clockwise, upper chains when it is not strictly clockwise
-__device__ __forceinline__ bool drop(int side, const float2 &a, const float2 &b, const float2 &c)
-{
-    const int o = orient(a.x, a.y, b.x, b.y, c.x, c.y);
-    return side == 0 ? o <= 0 : o >= 0;
-}
+// Values written by other blocks are read through L2 (ld.cg): this
+// thread's L1 may hold stale lines.
+struct GlobalAcc {
+    const ChainPtrs &P;
+    __device__ int lo(int side, int c) const { return __ldcg(P.lo[side] + c); }
+    __device__ int hi(int side, int c) const { return __ldcg(P.hi[side] + c); }
+    __device__ int prv(int side, int c) const { return __ldcg(P.prv[side] + c); }
+    __device__ int nxt(int side, int c) const { return __ldcg(P.nxt[side] + c); }
+    __device__ void set_range(int side, int c, int l, int h) const
+    {
+        P.lo[side][c] = l;
+        P.hi[side][c] = h;
+    }
+    __device__ void set_lo(int side, int c, int l) const { P.lo[side][c] = l; }
+    __device__ void set_hi(int side, int c, int h) const { P.hi[side][c] = h; }
+    __device__ void link(int side, int a, int b) const
+    {
+        P.nxt[side][a] = b;
+        P.prv[side][b] = a;
+    }
+    __device__ float2 point(int side, int c, int k) const { return __ldcg(P.pt[side] + (int64_t)c * CS + k); }
+};
 
-// first / last live chunk of tree node (level, j); level 0 = chunk j
+// first / last live super-chunk of tree node (level, j); level 0 = super-chunk j
 __device__ __forceinline__ void node_ends(const ChainPtrs &P, int level, int64_t nb, int64_t j, int side,
                                           int32_t &first, int32_t &last)
 {
     if (level == 0) {
-        const bool live = ldcg(P.hi[side] + j) >= ldcg(P.lo[side] + j);
+        const bool live = __ldcg(P.hi[side] + j) >= __ldcg(P.lo[side] + j);
         first = last = live ? (int32_t)j : -1;
     } else {
-        first = ldcg(P.node + (nb + j) * 4 + 2 * side);
-        last = ldcg(P.node + (nb + j) * 4 + 2 * side + 1);
+        first = __ldcg(P.node + (nb + j) * 4 + 2 * side);
+        last = __ldcg(P.node + (nb + j) * 4 + 2 * side + 1);
     }
 }
 
-__device__ void merge_side(const ChainPtrs &P, int side, int32_t fa, int32_t la, int32_t fb, int32_t lb)
+// Climb the global tree from super-chunk c: the second child to arrive at a
+// node merges its two children and continues upward.
+__device__ void climb(const ChainPtrs &P, int64_t c, int64_t nsc)
 {
-    int32_t *lo = P.lo[side], *hi = P.hi[side], *prv = P.prv[side], *nxt = P.nxt[side];
-    int32_t ca = la, ka = ldcg(hi + ca);
-    int32_t cb = fb, kb = ldcg(lo + cb);
-    int32_t hia = ka, lob = kb;          // live range ends of the current chunks
-    int32_t loa = ldcg(lo + ca), hib = ldcg(hi + cb);
-    float2 pa = vertex(P, side, ca, ka);
-    float2 pb = vertex(P, side, cb, kb);
-    for (;;) {
-        bool moved = false;
-        for (;;) {   // advance b
-            int32_t nc_ = cb, nk = kb + 1;
-            int32_t nlo = lob, nhi = hib;
-            if (kb >= hib) {
-                if (cb == lb) break;
-                nc_ = ldcg(nxt + cb);
-                nlo = ldcg(lo + nc_);
-                nhi = ldcg(hi + nc_);
-                nk = nlo;
+    GlobalAcc G{P};
+    int64_t node = c, w = nsc, nb_child = 0, nb = 0;   // nb: base of the level above
+    int level = 0;
+    while (w > 1) {
+        const int64_t parent = node >> 1, pw = (w + 1) / 2;
+        const int64_t sib = node ^ 1;
+        int32_t rec[4];
+        if (sib >= w) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side)
+                node_ends(P, level, nb_child, node, side, rec[2 * side], rec[2 * side + 1]);
+        } else {
+            __threadfence();
+            if (atomicAdd(P.node_cnt + nb + parent, 1) == 0) return;   // first to arrive: the sibling merges
+            __threadfence();
+            const int64_t a = parent * 2, b = a + 1;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                int32_t fa, la, fb, lb;
+                node_ends(P, level, nb_child, a, side, fa, la);
+                node_ends(P, level, nb_child, b, side, fb, lb);
+                if (la < 0) {
+                    rec[2 * side] = fb;
+                    rec[2 * side + 1] = lb;
+                } else if (fb < 0) {
+                    rec[2 * side] = fa;
+                    rec[2 * side + 1] = la;
+                } else {
+                    merge_walk(G, side, fa, la, fb, lb);
+                    rec[2 * side] = fa;
+                    rec[2 * side + 1] = lb;
+                }
             }
-            const float2 q = vertex(P, side, nc_, nk);
-            if (!drop(side, pa, pb, q)) break;
-            if (nc_ != cb) {          // chunk cb is now entirely removed
-                lo[cb] = 1;
-                hi[cb] = 0;
-                cb = nc_;
-                lob = nlo;
-                hib = nhi;
-            }
-            kb = nk;
-            pb = q;
-            moved = true;
         }
-        for (;;) {   // retreat a
-            int32_t pc = ca, pk = ka - 1;
-            int32_t plo = loa, phi = hia;
-            if (ka <= loa) {
-                if (ca == fa) break;
-                pc = ldcg(prv + ca);
-                plo = ldcg(lo + pc);
-                phi = ldcg(hi + pc);
-                pk = phi;
-            }
-            const float2 q = vertex(P, side, pc, pk);
-            if (!drop(side, q, pa, pb)) break;
-            if (pc != ca) {
-                lo[ca] = 1;
-                hi[ca] = 0;
-                ca = pc;
-                loa = plo;
-                hia = phi;
-            }
-            ka = pk;
-            pa = q;
-            moved = true;
-        }
-        if (!moved) break;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) P.node[(nb + parent) * 4 + f] = rec[f];
+        node = parent;
+        nb_child = nb;
+        nb += pw;
+        w = pw;
+        ++level;
     }
-    hi[ca] = ka;
-    lo[cb] = kb;
-    nxt[ca] = cb;
-    prv[cb] = ca;
 }
 
-__global__ void __launch_bounds__(kChainThreads) chain_kernel(void *ws, Layout L)
+// Block reduction of (y, position) pairs: the lowest (highest) y, ties to the
+// lowest position.  Contains two barriers.
+__device__ __forceinline__ void block_extreme_y(ChainSmem &s, float ylo, uint32_t qlo, float yhi, uint32_t qhi,
+                                                float &out_ylo, uint32_t &out_qlo, float &out_yhi, uint32_t &out_qhi)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float y1 = __shfl_xor_sync(0xffffffffu, ylo, o);
+        const uint32_t q1 = __shfl_xor_sync(0xffffffffu, qlo, o);
+        if (y1 < ylo || (y1 == ylo && q1 < qlo)) {
+            ylo = y1;
+            qlo = q1;
+        }
+        const float y2 = __shfl_xor_sync(0xffffffffu, yhi, o);
+        const uint32_t q2 = __shfl_xor_sync(0xffffffffu, qhi, o);
+        if (y2 > yhi || (y2 == yhi && q2 < qhi)) {
+            yhi = y2;
+            qhi = q2;
+        }
+    }
+    if (lane == 0) {
+        s.red_y[0][warp] = ylo;
+        s.red_q[0][warp] = qlo;
+        s.red_y[1][warp] = yhi;
+        s.red_q[1][warp] = qhi;
+    }
+    __syncthreads();
+    out_ylo = s.red_y[0][0];
+    out_qlo = s.red_q[0][0];
+    out_yhi = s.red_y[1][0];
+    out_qhi = s.red_q[1][0];
+    for (int w = 1; w < LT / 32; ++w) {
+        if (s.red_y[0][w] < out_ylo || (s.red_y[0][w] == out_ylo && s.red_q[0][w] < out_qlo)) {
+            out_ylo = s.red_y[0][w];
+            out_qlo = s.red_q[0][w];
+        }
+        if (s.red_y[1][w] > out_yhi || (s.red_y[1][w] == out_yhi && s.red_q[1][w] < out_qhi)) {
+            out_yhi = s.red_y[1][w];
+            out_qhi = s.red_q[1][w];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    if (s == 0) return;
+    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
+    const int64_t nsc = ceil_div((int64_t)s, SC);
+    const int t = threadIdx.x;
+    const float kInf = __int_as_float(0x7f800000);
+
+    for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
+        const int64_t base = sc * SC;
+        const int m = (int)min((int64_t)SC, (int64_t)s - base);
+        // ---- stage the super-chunk (coalesced), decoded to points
+        for (int i = t; i < m; i += LT) sm.pts[i] = sorted_point(P, base + i);
+        if (t == 0) {
+            sm.has_prev = base > 0;
+            sm.prev_x = base > 0 ? key_float(__ldg(P.keys + base - 1)) : 0.0f;
+        }
+        __syncthreads();
+
+        // ---- runs of equal x that start in this super-chunk
+        const int R = block_compact(
+            sm, m,
+            [&](int i) {
+                return i == 0 ? !(sm.has_prev && sm.pts[0].x == sm.prev_x) : sm.pts[i].x != sm.pts[i - 1].x;
+            },
+            [](int i) { return (uint16_t)i; }, sm.list[2]);
+        if (R == 0) {   // the whole super-chunk continues an earlier run
+            if (t == 0)
+                for (int side = 0; side < 2; ++side) {
+                    P.lo[side][sc] = 0;
+                    P.hi[side][sc] = -1;
+                }
+            __syncthreads();
+            continue;
+        }
+        // ---- look ahead when the last run continues past the super-chunk
+        const float xr = sm.pts[m - 1].x;
+        const bool ext = base + m < (int64_t)s && key_float(__ldg(P.keys + base + m)) == xr;
+        int64_t run_end = base + m;
+        if (ext) {
+            float ylo = kInf, yhi = -kInf;
+            uint32_t qlo = 0xffffffffu, qhi = 0xffffffffu;
+            for (int64_t q0 = base + m;; q0 += LT) {
+                const int64_t q = q0 + t;
+                const bool in_run = q < (int64_t)s && key_float(__ldg(P.keys + q)) == xr;
+                if (in_run) {
+                    const float y = key_float((uint32_t)(__ldg(P.pay + q) >> 32));
+                    if (y < ylo || (y == ylo && (uint32_t)q < qlo)) {
+                        ylo = y;
+                        qlo = (uint32_t)q;
+                    }
+                    if (y > yhi || (y == yhi && (uint32_t)q < qhi)) {
+                        yhi = y;
+                        qhi = (uint32_t)q;
+                    }
+                }
+                // the keys are sorted, so the run's positions are contiguous
+                const int n_in = __syncthreads_count(in_run);
+                if (n_in < LT) {
+                    run_end = q0 + n_in;
+                    break;
+                }
+            }
+            float oyl, oyh;
+            uint32_t oql, oqh;
+            block_extreme_y(sm, ylo, qlo, yhi, qhi, oyl, oql, oyh, oqh);
+            if (t == 0) {
+                sm.pts[SC] = make_float2(xr, oyl);
+                sm.pts[SC + 1] = make_float2(xr, oyh);
+                sm.ext_pos[0] = oql;
+                sm.ext_pos[1] = oqh;
+            }
+        }
+        const bool holds_last = run_end == (int64_t)s;
+        __syncthreads();
+        // ---- representatives: lowest (list[0]) and highest (list[1]) point of each run
+        for (int k = t; k < R; k += LT) {
+            const int r0 = sm.list[2][k];
+            const int r1 = k + 1 < R ? sm.list[2][k + 1] : m;
+            int lo = r0, hi = r0;
+            float ylo = sm.pts[r0].y, yhi = ylo;
+            for (int i = r0 + 1; i < r1; ++i) {
+                const float y = sm.pts[i].y;
+                if (y < ylo) {
+                    ylo = y;
+                    lo = i;
+                }
+                if (y > yhi) {
+                    yhi = y;
+                    hi = i;
+                }
+            }
+            if (k == R - 1 && ext) {
+                if (sm.pts[SC].y < ylo) lo = SC;
+                if (sm.pts[SC + 1].y > yhi) hi = SC + 1;
+            }
+            sm.list[0][k] = (uint16_t)lo;
+            sm.list[1][k] = (uint16_t)hi;
+        }
+        __syncthreads();
+        const uint16_t first_lo = sm.list[0][0];
+        const bool first_two = base == 0 && sm.pts[sm.list[1][0]].y > sm.pts[first_lo].y;
+
+        for (int side = 0; side < 2; ++side) {
+            // ---- this side's sequence in list[0]
+            if (side == 0) {
+                // lowest of every run, then the highest of the very last run
+                if (t == 0) {
+                    int len = R;
+                    if (holds_last && sm.pts[sm.list[1][R - 1]].y > sm.pts[sm.list[0][R - 1]].y)
+                        sm.list[0][len++] = sm.list[1][R - 1];
+                    sm.seq_len = len;
+                }
+            } else {
+                // the lowest of the very first run, then the highest of every run
+                const int off = first_two ? 1 : 0;
+                for (int k = t; k < R; k += LT) sm.list[0][k + off] = sm.list[1][k];
+                if (t == 0) {
+                    if (first_two) sm.list[0][0] = first_lo;
+                    sm.seq_len = R + off;
+                }
+            }
+            __syncthreads();
+            int len = sm.seq_len;
+            // ---- elimination passes: keep the ends and the strict turns
+            int cur = 0;
+            for (int pass = 0; pass < kElimPasses && len > 2; ++pass) {
+                const uint16_t *src = sm.list[cur];
+                const int n_old = len;
+                len = block_compact(
+                    sm, n_old,
+                    [&](int j) {
+                        if (j == 0 || j == n_old - 1) return true;
+                        return !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
+                    },
+                    [&](int j) { return src[j]; }, sm.list[cur == 0 ? 2 : 0]);
+                cur = cur == 0 ? 2 : 0;
+                if (len == n_old) break;
+            }
+            const uint16_t *lst = sm.list[cur];
+
+            // ---- leaf chain over sequence positions [t * LC, t * LC + cnt)
+            const int cnt = max(0, min(LC, len - t * LC));
+            int h = 0;
+            float2 t1 = make_float2(0.0f, 0.0f), t2 = t1;   // top and second of the stack
+            for (int k = 0; k < cnt; ++k) {
+                const float2 p = sm.pts[lst[t * LC + k]];
+                while (h >= 2 && drop(side, t2, t1, p)) {
+                    --h;
+                    t1 = t2;
+                    if (h >= 2) t2 = sm.pts[lst[t * LC + sm.stk[(h - 2) * LT + t]]];
+                }
+                sm.stk[h * LT + t] = (uint8_t)k;
+                ++h;
+                t2 = t1;
+                t1 = p;
+            }
+            sm.lo[t] = 0;
+            sm.hi[t] = (int16_t)(h - 1);
+            sm.first[t] = sm.last[t] = (int16_t)(h > 0 ? t : -1);
+            __syncthreads();
+
+            // ---- in-block merge tree over the leaves
+            SmemAcc A{sm, lst};
+            for (int w = 1; w < LT; w *= 2) {
+                if (t < LT / (2 * w)) {
+                    const int a0 = 2 * t * w, b0 = a0 + w;
+                    const int fa = sm.first[a0], la = sm.last[a0];
+                    const int fb = sm.first[b0], lb = sm.last[b0];
+                    if (la >= 0 && fb >= 0) merge_walk(A, side, fa, la, fb, lb);
+                    sm.first[a0] = (int16_t)(la >= 0 ? fa : fb);
+                    sm.last[a0] = (int16_t)(fb >= 0 ? lb : la);
+                }
+                __syncthreads();
+            }
+
+            // ---- write the super-chunk's chain contiguously
+            const int l = sm.lo[t], hh = sm.hi[t];
+            const int c = hh >= l ? hh - l + 1 : 0;
+            const int off = (int)block_scan(sm, (uint32_t)c);
+            uint32_t *dpos = P.pos[side] + sc * CS + off;
+            float2 *dpt = P.pt[side] + sc * CS + off;
+            for (int q = 0; q < c; ++q) {
+                const int e = lst[t * LC + sm.stk[(l + q) * LT + t]];
+                dpos[q] = e < SC ? (uint32_t)(base + e) : sm.ext_pos[e - SC];
+                dpt[q] = sm.pts[e];
+            }
+            if (t == 0) {
+                P.lo[side][sc] = 0;
+                P.hi[side][sc] = (int)sm.total - 1;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Global merge tree over the super-chunks: one thread per super-chunk
+// climbs; the second child to reach a node merges the pair.
+__global__ void __launch_bounds__(32) chain_merge_kernel(void *ws, Layout L)
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
     const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
-    const int64_t nc = ceil_div((int64_t)s, C);
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gthreads) {
-        // ---- leaf: sequential monotone chain over the chunk
-        const int64_t begin = c * C;
-        const int64_t end = min(begin + C, (int64_t)s);
-        unsigned long long prev_key = begin > 0 ? __ldg(P.keys + begin - 1) : ~0ull;
-        bool have_prev = begin > 0;
-        int32_t h[2] = {0, 0};
-        float2 t1[2], t2[2];   // top and second of each stack
-        for (int64_t k = begin; k < end; ++k) {
-            const unsigned long long key = __ldg(P.keys + k);
-            if (have_prev && key == prev_key) continue;
-            have_prev = true;
-            prev_key = key;
-            const float2 p = key_point(key);
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                uint32_t *st = P.chain[side] + begin;
-                while (h[side] >= 2 && drop(side, t2[side], t1[side], p)) {
-                    --h[side];
-                    t1[side] = t2[side];
-                    if (h[side] >= 2) t2[side] = key_point(__ldg(P.keys + st[h[side] - 2]));
-                }
-                st[h[side]] = (uint32_t)k;
-                ++h[side];
-                t2[side] = t1[side];
-                t1[side] = p;
-            }
-        }
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            P.lo[side][c] = 0;
-            P.hi[side][c] = h[side] - 1;
-        }
-
-        // ---- climb: the second child to arrive merges the pair
-        int64_t node = c, w = nc, nb_child = 0, nb = 0;   // nb: base of the level above
-        int level = 0;
-        while (w > 1) {
-            const int64_t parent = node >> 1, pw = (w + 1) / 2;
-            const int64_t sib = node ^ 1;
-            int32_t rec[4];
-            if (sib >= w) {
-                // no sibling: the parent is this node
-#pragma unroll
-                for (int side = 0; side < 2; ++side) node_ends(P, level, nb_child, node, side, rec[2 * side], rec[2 * side + 1]);
-            } else {
-                __threadfence();
-                if (atomicAdd(P.node_cnt + nb + parent, 1) == 0) break;   // first to arrive: the sibling merges
-                __threadfence();
-                const int64_t a = parent * 2, b = a + 1;
-#pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    int32_t fa, la, fb, lb;
-                    node_ends(P, level, nb_child, a, side, fa, la);
-                    node_ends(P, level, nb_child, b, side, fb, lb);
-                    if (la < 0) {
-                        rec[2 * side] = fb;
-                        rec[2 * side + 1] = lb;
-                    } else if (fb < 0) {
-                        rec[2 * side] = fa;
-                        rec[2 * side + 1] = la;
-                    } else {
-                        merge_side(P, side, fa, la, fb, lb);
-                        rec[2 * side] = fa;
-                        rec[2 * side + 1] = lb;
-                    }
-                }
-            }
-#pragma unroll
-            for (int f = 0; f < 4; ++f) P.node[(nb + parent) * 4 + f] = rec[f];
-            node = parent;
-            nb_child = nb;
-            nb += pw;
-            w = pw;
-            ++level;
-        }
-    }
+    const int64_t nsc = ceil_div((int64_t)s, SC);
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nsc) climb(P, c, nsc);
 }
 
-// Compacts the live chain ranges: thread = chunk, look-back over chunk
-// tiles, warp-cooperative copies.  Side 0 goes to hull_idx, side 1 to utmp.
+// Compacts the live chain ranges: thread = super-chunk, look-back over
+// tiles of super-chunks, warp-cooperative copies.  Side 0 goes to
+// hull_idx, side 1 to utmp.
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, uint32_t *hull_idx)
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
@@ -254,7 +633,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
     const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
-    const int64_t nc = ceil_div((int64_t)s, C);
+    const int64_t nc = ceil_div((int64_t)s, SC);
     const int64_t ntiles = ceil_div(nc, kEmitThreads);
     uint32_t *utmp = at<uint32_t>(ws, L.utmp);
     unsigned long long *status[2] = {at<unsigned long long>(ws, L.emit_status[0]),
@@ -274,8 +653,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
         if (c < nc) {
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                lo[side] = ldcg(P.lo[side] + c);
-                const int32_t hi = ldcg(P.hi[side] + c);
+                lo[side] = __ldcg(P.lo[side] + c);
+                const int32_t hi = __ldcg(P.hi[side] + c);
                 cnt[side] = hi >= lo[side] ? hi - lo[side] + 1 : 0;
             }
         }
@@ -324,7 +703,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
         for (int side = 0; side < 2; ++side) {
             const uint64_t mypos = s_excl[side] + s_wsum[side][warp] + pre[side];
             uint32_t *out = side == 0 ? hull_idx : utmp;
-            const uint32_t *chain = P.chain[side];
+            const uint32_t *chain = P.pos[side];
             for (int i = 0; i < 32; ++i) {
                 const int32_t n_i = __shfl_sync(0xffffffffu, cnt[side], i);
                 if (n_i == 0) continue;
@@ -332,8 +711,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
                 const uint64_t pos_i = __shfl_sync(0xffffffffu, mypos, i);
                 const int64_t ci = tile * kEmitThreads + warp * 32 + i;
                 for (int32_t k = (int32_t)lane; k < n_i; k += 32) {
-                    const uint32_t sp = __ldcg(chain + ci * C + lo_i + k);
-                    if (pos_i + k < (uint64_t)s) out[pos_i + k] = __ldg(P.vals + sp);
+                    const uint32_t sp = __ldcg(chain + ci * CS + lo_i + k);
+                    if (pos_i + k < (uint64_t)s) out[pos_i + k] = (uint32_t)__ldg(P.pay + sp);
                 }
             }
         }
@@ -359,11 +738,19 @@ __global__ void finish_kernel(void *ws, Layout L, uint32_t *hull_idx, uint32_t *
 cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st)
 {
     const int sms = sm_count();
-    int64_t cb = ceil_div(L.n_chunks, kChainThreads);
-    if (cb > (int64_t)sms * 16) cb = (int64_t)sms * 16;
+    int64_t cb = L.n_chunks;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChainSmem));
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, chain_kernel, LT, sizeof(ChainSmem));
+        per_sm = v > 0 ? v : 1;
+    }
+    if (cb > (int64_t)sms * per_sm) cb = (int64_t)sms * per_sm;
     if (cb < 1) cb = 1;
     probe_before(CH_K_CHAIN, st);
-    chain_kernel<<<(unsigned)cb, kChainThreads, 0, st>>>(ws, L);
+    chain_kernel<<<(unsigned)cb, LT, sizeof(ChainSmem), st>>>(ws, L);
+    chain_merge_kernel<<<(unsigned)ceil_div(L.n_chunks, 32), 32, 0, st>>>(ws, L);
     probe_after(CH_K_CHAIN, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

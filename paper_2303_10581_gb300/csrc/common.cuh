@@ -23,9 +23,12 @@ constexpr int kFiltTile = kFiltThreads * kFiltItems;   // 4096 points = 32 KB
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys
-constexpr int kSortPasses = 8;        // 64-bit keys, 8-bit digits
-constexpr int kChainC = 64;           // points per leaf chunk of the chain
-constexpr int kChainThreads = 128;
+constexpr int kSortPasses = 4;        // 32-bit x keys, 8-bit digits
+constexpr int kLeafC = 16;            // points per leaf chain (one thread)
+constexpr int kChainThreads = 256;    // leaves per super-chunk (one block)
+constexpr int kChainC = kLeafC * kChainThreads;   // 4096 points per super-chunk
+constexpr int kChainStride = kChainC + 8;          // chain slots per super-chunk (up to kChainC + 1 used)
+constexpr int kElimPasses = 12;       // cap on the parallel elimination passes
 constexpr int kEmitThreads = 256;     // chunks per emit tile (one per thread)
 constexpr int64_t kMaxHullN = (int64_t)1 << 30;
 constexpr int64_t kMaxN = ((int64_t)1 << 32) - 1;
@@ -98,17 +101,18 @@ struct Persist {
 struct Layout {
     size_t persist, extctrl, oct, ext8;
     size_t ctrl;            // Ctrl, immediately followed by
-    size_t filt_status;     // u64[filt_tiles] and
-    size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node
-    size_t zero_words;      // u64 words from ctrl to the end of node_cnt
-    size_t keys[2];         // u64[n]
-    size_t vals[2];         // u32[n]
+    size_t filt_status;     // u64[filt_tiles],
+    size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node, and
+    size_t emit_status[2];  // u64[emit_tiles]: look-back of the chain compaction
+    size_t zero_words;      // u64 words from ctrl to the end of emit_status[1]
+    size_t keys[2];         // u32[n]: ord(x) of each survivor (sort key)
+    size_t pay[2];          // u64[n]: ord(y) << 32 | point index (sort payload)
     size_t sort_status[2];  // u32[sort_tiles * 256]
-    size_t chainL, chainU;  // u32[n_chunks * C]
+    size_t chain_pos[2];    // u32[n_chunks * kChainStride]: sorted positions of chain vertices
+    size_t chain_pt[2];     // float2[n_chunks * kChainStride]: their coordinates
     size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
     size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
-    size_t emit_status[2];  // u64[emit_tiles]
-    size_t utmp;            // u32[n]
+    size_t utmp;           // u32[n]
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
 };
@@ -151,19 +155,21 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     L.ctrl = take(sizeof(Ctrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
     L.node_cnt = take((size_t)L.n_nodes * 4);
-    L.zero_words = (L.node_cnt + (size_t)L.n_nodes * 4 - L.ctrl + 7) / 8;
-    L.keys[0] = take((size_t)n * 8);
-    L.keys[1] = take((size_t)n * 8);
-    L.vals[0] = take((size_t)n * 4);
-    L.vals[1] = take((size_t)n * 4);
-    L.sort_status[0] = take((size_t)L.sort_tiles * 256 * 4);
-    L.sort_status[1] = take((size_t)L.sort_tiles * 256 * 4);
-    L.chainL = take((size_t)L.n_chunks * kChainC * 4);
-    L.chainU = take((size_t)L.n_chunks * kChainC * 4);
-    L.chunk = take((size_t)L.n_chunks * 8 * 4);
-    L.node = take((size_t)L.n_nodes * 4 * 4);
     L.emit_status[0] = take((size_t)L.emit_tiles * 8);
     L.emit_status[1] = take((size_t)L.emit_tiles * 8);
+    L.zero_words = (L.emit_status[1] + (size_t)L.emit_tiles * 8 - L.ctrl + 7) / 8;
+    L.keys[0] = take((size_t)n * 4);
+    L.keys[1] = take((size_t)n * 4);
+    L.pay[0] = take((size_t)n * 8);
+    L.pay[1] = take((size_t)n * 8);
+    L.sort_status[0] = take((size_t)L.sort_tiles * 256 * 4);
+    L.sort_status[1] = take((size_t)L.sort_tiles * 256 * 4);
+    for (int side = 0; side < 2; ++side) {
+        L.chain_pos[side] = take((size_t)L.n_chunks * kChainStride * 4);
+        L.chain_pt[side] = take((size_t)L.n_chunks * kChainStride * 8);
+    }
+    L.chunk = take((size_t)L.n_chunks * 8 * 4);
+    L.node = take((size_t)L.n_nodes * 4 * 4);
     L.utmp = take((size_t)n * 4);
     L.total = o;
     return L;
@@ -278,13 +284,43 @@ static __device__ __noinline__ int orient_d(float ax, float ay, float bx, float 
     return orient_exact(ax, ay, bx, by, cx, cy);
 }
 
+// Sterbenz: a - c is exact in binary32 when a and c have the same sign and
+// are within a factor of two of each other.
+__device__ __forceinline__ bool exact_diff(float a, float c)
+{
+    const float aa = fabsf(a), cc = fabsf(c);
+    return ((a >= 0.0f) == (c >= 0.0f)) && aa <= 2.0f * cc && cc <= 2.0f * aa;
+}
+
+// Tier 1b: exact binary32 sign for nearby points.  When the four
+// differences are exact, detleft = u1 v1 and detright = u2 v2 exactly; with
+// p = fl(u v) and e = fma(u, v, -p) = u v - p (exact while |p| >= 2^-100 or
+// a factor is zero, since then the product cannot underflow), rounding is
+// monotone, so p1 > p2 implies u1 v1 > u2 v2, and when p1 == p2 the
+// determinant is e1 - e2, whose sign survives the one rounding of
+// fl(e1 - e2).  Returns 2 when the preconditions do not hold.
+__device__ __forceinline__ int orient_near(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    if (!(exact_diff(ax, cx) && exact_diff(by, cy) && exact_diff(ay, cy) && exact_diff(bx, cx))) return 2;
+    const float u1 = __fsub_rn(ax, cx), v1 = __fsub_rn(by, cy);
+    const float u2 = __fsub_rn(ay, cy), v2 = __fsub_rn(bx, cx);
+    const float p1 = __fmul_rn(u1, v1), p2 = __fmul_rn(u2, v2);
+    const bool ok1 = (u1 == 0.0f || v1 == 0.0f) || (fabsf(p1) >= 7.888609052210118e-31f /* 2^-100 */ &&
+                                                    fabsf(p1) <= 3.0e38f);
+    const bool ok2 = (u2 == 0.0f || v2 == 0.0f) || (fabsf(p2) >= 7.888609052210118e-31f && fabsf(p2) <= 3.0e38f);
+    if (!(ok1 && ok2)) return 2;
+    if (p1 != p2) return p1 > p2 ? 1 : -1;
+    const float d = __fsub_rn(__fmaf_rn(u1, v1, -p1), __fmaf_rn(u2, v2, -p2));
+    return d > 0.0f ? 1 : (d < 0.0f ? -1 : 0);
+}
+
 // Tier 1: binary32 evaluation with a dynamic bound.  The expression has
 // Shewchuk's orient2d shape (four differences, two products, one
 // subtraction), whose rounding error is below (3 + 16 eps) eps * detsum with
 // eps = 2^-24 when nothing under- or overflows; 4 eps * detsum leaves room
 // for the rounding of the bound itself, and 2^-140 absorbs the absolute
-// error of products that fall into the subnormal range.  Non-finite or
-// undecided cases go to tier 2.
+// error of products that fall into the subnormal range.  Undecided cases
+// try tier 1b, then tier 2.
 __device__ __forceinline__ int orient(float ax, float ay, float bx, float by, float cx, float cy)
 {
     float detleft = __fmul_rn(__fsub_rn(ax, cx), __fsub_rn(by, cy));
@@ -296,6 +332,8 @@ __device__ __forceinline__ int orient(float ax, float ay, float bx, float by, fl
         if (det > eb) return 1;
         if (-det > eb) return -1;
     }
+    const int o = orient_near(ax, ay, bx, by, cx, cy);
+    if (o != 2) return o;
     return orient_d(ax, ay, bx, by, cx, cy);
 }
 

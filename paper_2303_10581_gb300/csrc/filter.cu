@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
 
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
-    unsigned long long *out_keys = at<unsigned long long>(ws, L.keys[0]);
-    uint32_t *out_vals = at<uint32_t>(ws, L.vals[0]);
+    uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
+    unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
 
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(at<Octagon>(ws, L.oct));
@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
                         const int64_t pos = (int64_t)excl + pre;
                         const uint32_t idx = (uint32_t)(base + (int64_t)(r * kFiltThreads + tid) * G + h);
                         if constexpr (KEYS) {
-                            out_keys[pos] = point_key(px[r * G + h], py[r * G + h]);
-                            out_vals[pos] = idx;
+                            out_keys[pos] = ord_key(px[r * G + h]);
+                            out_pay[pos] = ((unsigned long long)ord_key(py[r * G + h]) << 32) | idx;
                         } else {
                             surv_idx[pos] = idx;
                             if (surv_pts) surv_pts[pos] = make_float2(px[r * G + h], py[r * G + h]);

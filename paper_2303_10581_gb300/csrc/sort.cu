@@ -1,19 +1,25 @@
-// sort.cu -- stable LSD radix sort of the survivors by (x, y) for the
-// monotone chain of Sec. 3.3 (Andrew's algorithm starts from the points in
+// sort.cu -- stable LSD radix sort of the survivors by x for the monotone
+// chain of Sec. 3.3 (Andrew's algorithm starts from the points in
 // lexicographic order; the paper leaves this step to a CPU library).
 //
-// Keys are (ord(x) << 32 | ord(y)) with ord() the order-preserving map of
-// binary32 to uint32 (-0 mapped to +0), values are the original point
-// indices.  The filter writes the pairs in ascending index order and every
-// pass is stable, so equal points end up in ascending index order.
+// Only x is sorted: the key is ord(x), the order-preserving map of binary32
+// to uint32 (-0 mapped to +0), and the payload is (ord(y) << 32 | index).
+// Among points of equal x only the lowest can be a lower-chain vertex and
+// only the highest an upper-chain vertex (apart from the first and last x),
+// so the chain kernel reduces each equal-x run itself and y never needs to
+// be part of the sort order.  That makes four 8-bit passes instead of eight.
+// The filter writes the pairs in ascending index order and every pass is
+// stable, so each equal-x run stays in ascending index order.
 //
 // Structure (one-sweep style, Adinets & Merrill 2022): one histogram kernel
-// computes all eight 8-bit digit histograms in a single read and marks
-// passes whose digit is constant (skipped); each remaining pass is one
-// persistent kernel that ranks a 4096-key tile in shared memory (warp
-// match_any ranking, stable), finds the tile's per-digit global offsets by
-// a decoupled look-back over 256 digit counters, and writes the tile out
-// digit-sorted, so stores are runs of consecutive addresses.
+// computes all four digit histograms in a single read and marks passes
+// whose digit is constant (skipped); each remaining pass is one persistent
+// kernel that ranks a 4096-key tile in shared memory (warp match_any
+// ranking, stable), finds the tile's per-digit global offsets by a
+// decoupled look-back over 256 digit counters, and writes the tile out
+// digit-sorted, so stores are runs of consecutive addresses.  The payload
+// is staged in shared memory in element order and gathered through the
+// tile's inverse permutation at write-out, so it never occupies registers.
 #include "common.cuh"
 #include "launch.h"
 
@@ -24,12 +30,13 @@ namespace {
 constexpr int NW = kSortThreads / 32;
 
 struct SortSmem {
-    unsigned long long keys[kSortTile];
-    uint32_t vals[kSortTile];
-    uint32_t wh[NW][256];      // per-warp digit counts, then per-warp offsets
-    uint32_t tstart[256];      // start of each digit inside the sorted tile
-    uint32_t gbase[256];       // output position of the tile's digit run, minus tstart
-    uint32_t dbase[256];       // global start of each digit (exclusive scan of the histogram)
+    unsigned long long pay[kSortTile];   // payload, element order
+    uint32_t keys[kSortTile];            // keys, digit-sorted order
+    uint16_t inv[kSortTile];             // digit-sorted position -> element
+    uint32_t wh[NW][256];                // per-warp digit counts, then per-warp offsets
+    uint32_t tstart[256];                // start of each digit inside the sorted tile
+    uint32_t gbase[256];                 // output position of the tile's digit run, minus tstart
+    uint32_t dbase[256];                 // global start of each digit (exclusive scan of the histogram)
     uint32_t warp_tot[NW];
     uint32_t tile;
 };
@@ -73,9 +80,19 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
     __shared__ bool s_last;
     for (int i = threadIdx.x; i < kSortPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
     __syncthreads();
-    const unsigned long long *keys = at<unsigned long long>(ws, L.keys[0]);
-    for (int64_t i = gtid; i < (int64_t)s; i += gthreads) {
-        const unsigned long long k = keys[i];
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const int64_t nq = (int64_t)s / 4;   // 16-byte vector loads
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+    for (int64_t i = gtid; i < nq; i += gthreads) {
+        const uint4 v = __ldcs(k4 + i);
+        const uint32_t kk[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int p = 0; p < kSortPasses; ++p) atomicAdd(&sh[p][(kk[q] >> (8 * p)) & 255u], 1u);
+    }
+    for (int64_t i = nq * 4 + gtid; i < (int64_t)s; i += gthreads) {
+        const uint32_t k = keys[i];
 #pragma unroll
         for (int p = 0; p < kSortPasses; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
     }
@@ -90,25 +107,26 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // a pass whose digit is the same for every key moves nothing: one
+    // thread per digit checks all passes at once
+    __shared__ int s_skip[kSortPasses];
+    if (threadIdx.x < kSortPasses) s_skip[threadIdx.x] = s <= 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSortPasses * 256; i += blockDim.x)
+        if (__ldcg(&(&ctrl->hist[0][0])[i]) == s) s_skip[i / 256] = 1;
+    __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t cur = 0;
         for (int p = 0; p < kSortPasses; ++p) {
-            bool skip = true;
-            for (int d = 0; d < 256; ++d) {
-                const uint32_t c = *(volatile uint32_t *)&ctrl->hist[p][d];
-                if (c != 0 && c != s) skip = false;
-                if (c == s) break;
-            }
-            if (s <= 1) skip = true;
-            ctrl->pass_skip[p] = skip;
+            ctrl->pass_skip[p] = s_skip[p];
             ctrl->pass_src[p] = cur;
-            if (!skip) cur ^= 1u;
+            if (!s_skip[p]) cur ^= 1u;
         }
         ctrl->final_buf = cur;
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(void *ws, Layout L, int p)
+__global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, Layout L, int p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
@@ -118,10 +136,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(void *ws, Layou
     if (s == 0 || ctrl->pass_skip[p]) return;
     const uint32_t src = ctrl->pass_src[p], dst = src ^ 1u;
     const int64_t ntiles = ceil_div((int64_t)s, kSortTile);
-    const unsigned long long *kin = at<unsigned long long>(ws, L.keys[src]);
-    const uint32_t *vin = at<uint32_t>(ws, L.vals[src]);
-    unsigned long long *kout = at<unsigned long long>(ws, L.keys[dst]);
-    uint32_t *vout = at<uint32_t>(ws, L.vals[dst]);
+    const uint32_t *kin = at<uint32_t>(ws, L.keys[src]);
+    const unsigned long long *pin = at<unsigned long long>(ws, L.pay[src]);
+    uint32_t *kout = at<uint32_t>(ws, L.keys[dst]);
+    unsigned long long *pout = at<unsigned long long>(ws, L.pay[dst]);
     uint32_t *status = at<uint32_t>(ws, L.sort_status[src]);
     uint32_t *status_next = at<uint32_t>(ws, L.sort_status[dst]);
     const int shift = 8 * p;
@@ -150,26 +168,25 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(void *ws, Layou
         const int64_t base = tile * kSortTile;
         const uint32_t tile_n = (uint32_t)min((int64_t)kSortTile, (int64_t)s - base);
 
-        unsigned long long k[kSortItems];
-        uint32_t v[kSortItems];
-        uint32_t rank[kSortItems];
+        // keys to registers, payload to shared memory (element order)
+        uint32_t k[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
             if (e < tile_n) {
                 k[j] = __ldcs(kin + base + e);
-                v[j] = __ldcs(vin + base + e);
+                sm.pay[e] = __ldcs(pin + base + e);
             } else {
-                k[j] = ~0ull;
-                v[j] = 0u;
+                k[j] = 0u;
             }
         }
         // stable rank inside the warp, items in element order (j, lane)
+        uint16_t rank[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
             const bool ok = e < tile_n;
-            const uint32_t d = ok ? (uint32_t)(k[j] >> shift) & 255u : 256u;
+            const uint32_t d = ok ? (k[j] >> shift) & 255u : 256u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t before = __popc(peers & lt);
             uint32_t cur = 0;
@@ -177,19 +194,16 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(void *ws, Layou
             __syncwarp();
             if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
             __syncwarp();
-            rank[j] = cur + before;
+            rank[j] = (uint16_t)(cur + before);
         }
         __syncthreads();
         // per digit: exclusive offsets across warps and the tile count
         uint32_t cnt = 0;
-        {
-            const uint32_t d = tid;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t c = sm.wh[w][d];
-                sm.wh[w][d] = cnt;
-                cnt += c;
-            }
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = sm.wh[w][tid];
+            sm.wh[w][tid] = cnt;
+            cnt += c;
         }
         uint32_t tstart;
         block_excl_scan256(cnt, tstart, sm.warp_tot);
@@ -226,25 +240,25 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(void *ws, Layou
             }
             sm.gbase[d] = sm.dbase[d] + excl - tstart;
         }
-        // stage the tile digit-sorted in shared memory
+        // digit-sorted keys and the inverse permutation
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
             if (e < tile_n) {
-                const uint32_t d = (uint32_t)(k[j] >> shift) & 255u;
+                const uint32_t d = (k[j] >> shift) & 255u;
                 const uint32_t pos = sm.tstart[d] + sm.wh[warp][d] + rank[j];
                 sm.keys[pos] = k[j];
-                sm.vals[pos] = v[j];
+                sm.inv[pos] = (uint16_t)e;
             }
         }
         __syncthreads();
         for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-            const unsigned long long key = sm.keys[i];
-            const uint32_t d = (uint32_t)(key >> shift) & 255u;
+            const uint32_t key = sm.keys[i];
+            const uint32_t d = (key >> shift) & 255u;
             const uint32_t pos = sm.gbase[d] + i;
             if (pos < s) {   // always true unless a look-back wait gave up
                 kout[pos] = key;
-                vout[pos] = sm.vals[i];
+                pout[pos] = sm.pay[sm.inv[i]];
             }
         }
         __syncthreads();
