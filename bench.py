@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dists", default=",".join(ALL_DISTS),
                     help="subset of the workload's distributions (profiling runs)")
+    ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
+                    help="compaction schedule: 0 two passes, 1 single pass with look-back")
     return ap.parse_args()
 
 
@@ -225,6 +227,7 @@ def run_ours(args):
     host = make_inputs(n, args.seed)
     d_pts = [torch.from_numpy(p).to(dev) for p in host]
     ws = ch.Workspace(n, device=dev)
+    ch.ch_filter_variant(args.filter_variant)
     hull_idx = [torch.empty(n, dtype=torch.int32, device=dev) for _ in DISTS]
     hull_cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in DISTS]
     stream = torch.cuda.current_stream()

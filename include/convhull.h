@@ -127,6 +127,15 @@ ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32_t *ext8,
                             uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
                             void *stream);
 
+/* Compaction strategy of the filter (Sec. 3.2) for later ch_filter and
+ * ch_hull calls of this process; results are identical, only the schedule
+ * differs.  0 (default): two passes -- a streaming count of the survivors
+ * of every 4096-point tile, a scan of the counts, and a scatter pass that
+ * revisits only tiles with survivors.  1: one pass -- tiles in ticket order
+ * with a decoupled look-back for their output offsets.  CH_ERR_ARG for any
+ * other value.  Host-only. */
+ch_status ch_filter_variant(int32_t variant);
+
 /* ---- instrumentation (not part of the paper's method) ------------------
  * Kernel identifiers of the path, in launch order. */
 typedef enum {

@@ -31,7 +31,8 @@ STATUS = {
 CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOUT, CH_ERR_UNSUPPORTED = range(7)
 
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
-           "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc")
+           "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
+           "ch_filter_variant")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish")
 
 
@@ -71,6 +72,7 @@ def load(build_if_missing: bool = True):
     lib.ch_probe_start.argtypes = [ctypes.c_uint32, ctypes.c_int32]
     lib.ch_probe_stop.argtypes = [p, p]
     lib.ch_filter_noalloc.argtypes = [p, i64, p, p, p, p, p]
+    lib.ch_filter_variant.argtypes = [ctypes.c_int32]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -147,6 +149,12 @@ def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):
 def ch_last_error(ws, stream=None) -> int:
     """Synchronises the stream; returns (and clears) the device-side status."""
     return int(load().ch_last_error(_ptr(ws, "ws"), _stream(stream)))
+
+
+def ch_filter_variant(variant: int):
+    """Compaction schedule of the filter: 0 two passes (default), 1 single
+    pass with decoupled look-back.  Results are identical."""
+    _check(load().ch_filter_variant(int(variant)), "ch_filter_variant")
 
 
 def ch_probe_start(kernels=KERNELS, max_launches: int = 1024):

@@ -112,7 +112,8 @@ struct Layout {
     size_t chain_pt[2];     // float2[n_chunks * kChainStride]: their coordinates
     size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
     size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
-    size_t utmp;           // u32[n]
+    size_t keep_bits;       // u16[filt_tiles * kFiltThreads]: keep decisions of the count pass
+    size_t utmp;          // u32[n]
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
 };
@@ -170,6 +171,7 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     }
     L.chunk = take((size_t)L.n_chunks * 8 * 4);
     L.node = take((size_t)L.n_nodes * 4 * 4);
+    L.keep_bits = take((size_t)L.filt_tiles * kFiltThreads * 2);
     L.utmp = take((size_t)n * 4);
     L.total = o;
     return L;
@@ -335,6 +337,70 @@ __device__ __forceinline__ int orient(float ax, float ay, float bx, float by, fl
     const int o = orient_near(ax, ay, bx, by, cx, cy);
     if (o != 2) return o;
     return orient_d(ax, ay, bx, by, cx, cy);
+}
+
+// ---------------------------------------------------------------------------
+// bulk copies global -> shared (TMA, 1-D) completed on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisation visible to the async proxy (bulk copies).
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of transfer still to land.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory
+// before later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Copies `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// global to this CTA's shared memory; completion is signalled on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `parity` of `bar` to complete.  Returns false
+// when the limit is reached (the caller reports CH_ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // ---------------------------------------------------------------------------

@@ -1,15 +1,28 @@
 // filter.cu -- Sec. 3.2 of Carrasco et al.: buildingFilter (is a point
-// strictly inside the eight-vertex polygon?) fused with
-// compactingFilteredPoints (stable compaction of the kept points).
+// strictly inside the eight-vertex polygon?) and compactingFilteredPoints
+// (stable compaction of the kept points).
 //
 // The paper writes an n-entry flag vector, scans it (tensor-core segmented
-// scan, Thrust or CUB) and scatters.  Here one persistent kernel does it in
-// a single read of the points: each block takes 4096-point tiles in ticket
-// order, tests them, counts the kept points per (row, warp) with ballots,
-// publishes the tile count, obtains the tile's output offset with a
-// decoupled look-back, and writes the kept points in ascending index
-// order.  Flags never reach memory.  Memory traffic: 8 bytes per point read,
-// 12 bytes per kept point written.
+// scan, Thrust or CUB) and scatters.  Flags never reach memory here; two
+// variants are built:
+//
+//  * two-pass (default): a streaming count pass tests 4096-point tiles and
+//    writes one survivor count per tile; one block scans the counts into
+//    tile offsets; a scatter pass revisits only the tiles that have
+//    survivors, re-tests them (same arithmetic, same decisions) and writes
+//    the kept points in ascending index order.  No block waits on another,
+//    so every pass streams at memory speed; when almost everything is
+//    discarded (normal data) the points are read once, when nothing is
+//    (circle) they are read twice.
+//  * single-pass: one persistent kernel takes tiles in ticket order, tests
+//    them, publishes the tile count, gets its offset by decoupled look-back
+//    and writes its survivors; points are read once, but each tile waits on
+//    its predecessors.
+//
+// Memory traffic: 8 bytes per point read (twice for tiles with survivors in
+// the two-pass variant), 12 bytes per kept point written.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -50,134 +63,197 @@ __device__ __forceinline__ bool keep_point(const Octagon &o, float x, float y)
     return false;
 }
 
-// G points per thread per row (2 with 16-byte vector loads, 1 with 8-byte).
+constexpr int NW = kFiltThreads / 32;
+
+// Copies the polygon to shared memory; false when the call was aborted
+// (non-finite input or a bad vertex index).
+__device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout &L)
+{
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(at<Octagon>(ws, L.oct));
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&so);
+    for (uint32_t w = threadIdx.x; w < sizeof(Octagon) / 4; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    return !so.abort;
+}
+
+// Loads and tests one tile.  Thread t holds the points
+// base + (r * 256 + t) * G + h, r < kFiltItems / G, h < G (G = 2: one
+// 16-byte load per row; G = 1: one 8-byte load).  Returns the keep bits
+// (bit r * G + h); positions past n are not kept.
+template <int G>
+__device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int64_t n, int64_t base,
+                                              const Octagon &so, float (&px)[kFiltItems], float (&py)[kFiltItems])
+{
+    constexpr int ROWS = kFiltItems / G;
+    const uint32_t tid = threadIdx.x;
+    uint32_t keep = 0;
+    if (base + kFiltTile <= n) {
+        if constexpr (G == 2) {
+            const float4 *p4 = reinterpret_cast<const float4 *>(pts) + base / 2;
+            float4 v[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) v[r] = __ldcs(p4 + r * kFiltThreads + tid);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                px[2 * r] = v[r].x;
+                py[2 * r] = v[r].y;
+                px[2 * r + 1] = v[r].z;
+                py[2 * r + 1] = v[r].w;
+            }
+        } else {
+            const float2 *p2 = reinterpret_cast<const float2 *>(pts) + base;
+            float2 v[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) v[r] = __ldcs(p2 + r * kFiltThreads + tid);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                px[r] = v[r].x;
+                py[r] = v[r].y;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kFiltItems; ++q)
+            if (keep_point(so, px[q], py[q])) keep |= 1u << q;
+    } else {
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+            for (int h = 0; h < G; ++h) {
+                const int64_t i = base + (int64_t)(r * kFiltThreads + tid) * G + h;
+                px[r * G + h] = 0.0f;
+                py[r * G + h] = 0.0f;
+                if (i < n) {
+                    const float2 v = p2[i];
+                    px[r * G + h] = v.x;
+                    py[r * G + h] = v.y;
+                    if (keep_point(so, v.x, v.y)) keep |= 1u << (r * G + h);
+                }
+            }
+        }
+    }
+    return keep;
+}
+
+// Kept points per (row, warp), turned into exclusive offsets in row-major
+// order (the point order of the tile) in s_off by warp 0.  Returns the tile
+// total to warp 0.  The caller synchronises before and after.
+template <int G>
+__device__ __forceinline__ void row_counts(uint32_t keep, uint32_t (&s_off)[kFiltItems / G][NW])
+{
+    constexpr int ROWS = kFiltItems / G;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int h = 0; h < G; ++h) c += __popc(__ballot_sync(0xffffffffu, (keep >> (r * G + h)) & 1u));
+        if (lane == 0) s_off[r][warp] = c;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t scan_rows_warp0(uint32_t (&s_off)[kFiltItems / G][NW])
+{
+    constexpr int PER = (kFiltItems / G) * NW / 32;
+    const uint32_t lane = lane_id();
+    uint32_t *flat = &s_off[0][0];
+    uint32_t loc[PER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        loc[k] = flat[lane * PER + k];
+        sum += loc[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        flat[lane * PER + k] = run;
+        run += loc[k];
+    }
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Writes the kept points of one tile; excl is the tile's output offset.
+template <int G, bool KEYS>
+__device__ __forceinline__ void scatter_tile(uint32_t keep, int64_t base, uint64_t excl,
+                                             const uint32_t (&s_off)[kFiltItems / G][NW], const float (&px)[kFiltItems],
+                                             const float (&py)[kFiltItems], uint32_t *surv_idx, float2 *surv_pts,
+                                             uint32_t *out_keys, unsigned long long *out_pay)
+{
+    constexpr int ROWS = kFiltItems / G;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        uint32_t pre = s_off[r][warp];
+#pragma unroll
+        for (int h = 0; h < G; ++h) pre += __popc(__ballot_sync(0xffffffffu, (keep >> (r * G + h)) & 1u) & lt);
+#pragma unroll
+        for (int h = 0; h < G; ++h) {
+            if ((keep >> (r * G + h)) & 1u) {
+                const int64_t pos = (int64_t)excl + pre;
+                const uint32_t idx = (uint32_t)(base + (int64_t)(r * kFiltThreads + tid) * G + h);
+                if constexpr (KEYS) {
+                    out_keys[pos] = ord_key(px[r * G + h]);
+                    out_pay[pos] = ((unsigned long long)ord_key(py[r * G + h]) << 32) | idx;
+                } else {
+                    surv_idx[pos] = idx;
+                    if (surv_pts) surv_pts[pos] = make_float2(px[r * G + h], py[r * G + h]);
+                }
+                ++pre;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void write_count(bool keys, Ctrl *ctrl, uint32_t *surv_count, uint32_t v)
+{
+    if (keys) ctrl->surv_count = v;
+    else *surv_count = v;
+}
+
+// ---------------------------------------------------------------------------
+// single pass: ticket-ordered tiles with decoupled look-back
+// ---------------------------------------------------------------------------
 template <int G, bool KEYS>
 __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__restrict__ pts, int64_t n,
                                                               void *ws, Layout L, uint32_t *__restrict__ surv_idx,
                                                               float2 *__restrict__ surv_pts,
                                                               uint32_t *__restrict__ surv_count)
 {
-    constexpr int ROWS = kFiltItems / G;
-    constexpr int NW = kFiltThreads / 32;
     __shared__ Octagon so;
-    __shared__ uint32_t s_off[ROWS][NW];
+    __shared__ uint32_t s_off[kFiltItems / G][NW];
     __shared__ uint32_t s_tile;
     __shared__ unsigned long long s_excl;
     __shared__ uint32_t s_total;
 
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
-    uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
-    unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
-
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(at<Octagon>(ws, L.oct));
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&so);
-        for (uint32_t w = threadIdx.x; w < sizeof(Octagon) / 4; w += blockDim.x) dst[w] = src[w];
-    }
-    __syncthreads();
-    if (so.abort) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            if (KEYS) ctrl->surv_count = 0;
-            else if (surv_count) *surv_count = 0;
-        }
+    if (!load_octagon(so, ws, L)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) write_count(KEYS, ctrl, surv_count, 0);
         return;
     }
-
     const int64_t ntiles = ceil_div(n, kFiltTile);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    const uint32_t lt = (1u << lane) - 1u;
-
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&ctrl->filt_ticket, 1u);
         __syncthreads();
         const int64_t tile = s_tile;
         if (tile >= ntiles) break;
         const int64_t base = tile * kFiltTile;
-
-        float px[ROWS * G], py[ROWS * G];
-        uint32_t keep = 0;
-        if (base + kFiltTile <= n) {
-            if constexpr (G == 2) {
-                const float4 *p4 = reinterpret_cast<const float4 *>(pts) + base / 2;
-                float4 v[ROWS];
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) v[r] = __ldcs(p4 + r * kFiltThreads + tid);
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    px[r * G] = v[r].x;
-                    py[r * G] = v[r].y;
-                    px[r * G + G - 1] = v[r].z;
-                    py[r * G + G - 1] = v[r].w;
-                }
-            } else {
-                const float2 *p2 = reinterpret_cast<const float2 *>(pts) + base;
-                float2 v[ROWS];
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) v[r] = __ldcs(p2 + r * kFiltThreads + tid);
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) {
-                    px[r] = v[r].x;
-                    py[r] = v[r].y;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < ROWS * G; ++q)
-                if (keep_point(so, px[q], py[q])) keep |= 1u << q;
-        } else {
-            const float2 *p2 = reinterpret_cast<const float2 *>(pts);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-#pragma unroll
-                for (int h = 0; h < G; ++h) {
-                    const int64_t i = base + (int64_t)(r * kFiltThreads + tid) * G + h;
-                    if (i < n) {
-                        const float2 v = p2[i];
-                        px[r * G + h] = v.x;
-                        py[r * G + h] = v.y;
-                        if (keep_point(so, v.x, v.y)) keep |= 1u << (r * G + h);
-                    } else {
-                        px[r * G + h] = 0.0f;
-                        py[r * G + h] = 0.0f;
-                    }
-                }
-            }
-        }
-
-        // counts per (row, warp)
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int h = 0; h < G; ++h) c += __popc(__ballot_sync(0xffffffffu, (keep >> (r * G + h)) & 1u));
-            if (lane == 0) s_off[r][warp] = c;
-        }
+        float px[kFiltItems], py[kFiltItems];
+        const uint32_t keep = load_test<G>(pts, n, base, so, px, py);
+        row_counts<G>(keep, s_off);
         __syncthreads();
         if (warp == 0) {
-            // exclusive scan over (row, warp) in row-major order
-            constexpr int PER = ROWS * NW / 32;
-            uint32_t *flat = &s_off[0][0];
-            uint32_t loc[PER];
-            uint32_t sum = 0;
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                loc[k] = flat[lane * PER + k];
-                sum += loc[k];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += t;
-            }
-            uint32_t run = incl - sum;
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                flat[lane * PER + k] = run;
-                run += loc[k];
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            // publish, look back, publish the inclusive prefix
+            const uint32_t total = scan_rows_warp0<G>(s_off);
             unsigned long long excl = 0;
             if (tile == 0) {
                 if (lane == 0) st_release_u64(status, kFlagP | total);
@@ -189,83 +265,223 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
             if (lane == 0) {
                 s_excl = excl;
                 s_total = total;
-                if (tile == ntiles - 1) {
-                    if (KEYS) ctrl->surv_count = (uint32_t)(excl + total);
-                    else *surv_count = (uint32_t)(excl + total);
-                }
+                if (tile == ntiles - 1) write_count(KEYS, ctrl, surv_count, (uint32_t)(excl + total));
             }
         }
         __syncthreads();
-        if (s_total != 0) {
-            const unsigned long long excl = s_excl;
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                uint32_t pre = s_off[r][warp];
-                uint32_t b[G];
-#pragma unroll
-                for (int h = 0; h < G; ++h) {
-                    b[h] = __ballot_sync(0xffffffffu, (keep >> (r * G + h)) & 1u);
-                    pre += __popc(b[h] & lt);
-                }
-#pragma unroll
-                for (int h = 0; h < G; ++h) {
-                    if ((keep >> (r * G + h)) & 1u) {
-                        const int64_t pos = (int64_t)excl + pre;
-                        const uint32_t idx = (uint32_t)(base + (int64_t)(r * kFiltThreads + tid) * G + h);
-                        if constexpr (KEYS) {
-                            out_keys[pos] = ord_key(px[r * G + h]);
-                            out_pay[pos] = ((unsigned long long)ord_key(py[r * G + h]) << 32) | idx;
-                        } else {
-                            surv_idx[pos] = idx;
-                            if (surv_pts) surv_pts[pos] = make_float2(px[r * G + h], py[r * G + h]);
-                        }
-                        ++pre;
-                    }
-                }
-            }
-        }
+        if (s_total != 0)
+            scatter_tile<G, KEYS>(keep, base, s_excl, s_off, px, py, surv_idx, surv_pts, at<uint32_t>(ws, L.keys[0]),
+                                  at<unsigned long long>(ws, L.pay[0]));
         __syncthreads();
     }
 }
 
-template <int G, bool KEYS>
-int blocks_per_sm()
+// ---------------------------------------------------------------------------
+// two passes: count -> scan -> scatter
+// ---------------------------------------------------------------------------
+// filt_status[t] receives the survivor count of tile t (low 32 bits); the
+// scan turns it into (offset << 32 | count).  Each thread's 16 keep bits go
+// to keep_bits, so the scatter pass does not test again.
+template <int G>
+__global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float *__restrict__ pts, int64_t n,
+                                                                    void *ws, Layout L)
 {
-    static int cached = 0;
-    if (!cached) {
-        int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, filter_kernel<G, KEYS>, kFiltThreads, 0);
-        cached = v > 0 ? v : 1;
-    }
-    return cached;
-}
-
-template <int G, bool KEYS>
-cudaError_t launch_t(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx, float *surv_pts,
-                     uint32_t *surv_count, cudaStream_t st)
-{
+    __shared__ Octagon so;
+    __shared__ uint32_t s_w[NW];
+    if (!load_octagon(so, ws, L)) return;
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    int64_t blocks = (int64_t)sm_count() * blocks_per_sm<G, KEYS>();
-    if (blocks > ntiles) blocks = ntiles;
-    if (blocks < 1) blocks = 1;
-    probe_before(CH_K_FILTER, st);
-    filter_kernel<G, KEYS><<<(unsigned)blocks, kFiltThreads, 0, st>>>(
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        float px[kFiltItems], py[kFiltItems];
+        const uint32_t keep = load_test<G>(pts, n, tile * kFiltTile, so, px, py);
+        bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
+        uint32_t c = __popc(keep);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) s_w[warp] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) t += s_w[w];
+            status[tile] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// One block: exclusive scan of the tile counts, in place; the total is the
+// survivor count.
+__global__ void __launch_bounds__(1024) filter_scan_kernel(void *ws, Layout L, int64_t n, int keys,
+                                                           uint32_t *surv_count)
+{
+    __shared__ uint64_t s_w[32];
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    if (at<Octagon>(ws, L.oct)->abort) {
+        if (threadIdx.x == 0) write_count(keys, ctrl, surv_count, 0);
+        return;
+    }
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const int64_t ntiles = ceil_div(n, kFiltTile);
+    const int64_t per = ceil_div(ntiles, (int64_t)blockDim.x);
+    const int64_t t0 = threadIdx.x * per, t1 = min(t0 + per, ntiles);
+    uint64_t sum = 0;
+    for (int64_t t = t0; t < t1; ++t) sum += status[t] & 0xffffffffull;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint64_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint64_t before = 0, total = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+        if (w < warp) before += s_w[w];
+        total += s_w[w];
+    }
+    uint64_t run = before + incl - sum;
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint64_t c = status[t] & 0xffffffffull;
+        status[t] = (run << 32) | c;
+        run += c;
+    }
+    if (threadIdx.x == 0) write_count(keys, ctrl, surv_count, (uint32_t)total);
+}
+
+template <int G, bool KEYS>
+__global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const float *__restrict__ pts, int64_t n,
+                                                                      void *ws, Layout L,
+                                                                      uint32_t *__restrict__ surv_idx,
+                                                                      float2 *__restrict__ surv_pts)
+{
+    __shared__ uint32_t s_off[kFiltItems / G][NW];
+    __shared__ uint32_t s_abort;
+    if (threadIdx.x == 0) s_abort = at<Octagon>(ws, L.oct)->abort;
+    __syncthreads();
+    if (s_abort) return;
+    const unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
+    unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
+    const int64_t ntiles = ceil_div(n, kFiltTile);
+    const uint32_t tid = threadIdx.x;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const unsigned long long st = status[tile];
+        if ((st & 0xffffffffull) == 0) continue;   // block-uniform
+        const int64_t base = tile * kFiltTile;
+        const uint32_t keep = bits[tile * kFiltThreads + tid];
+        // coordinates of the kept points only (the decisions are stored)
+        float px[kFiltItems], py[kFiltItems];
+        constexpr int ROWS = kFiltItems / G;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            if constexpr (G == 2) {
+                px[2 * r] = py[2 * r] = px[2 * r + 1] = py[2 * r + 1] = 0.0f;
+                if ((keep >> (2 * r)) & 3u) {
+                    const int64_t i = base + (int64_t)(r * kFiltThreads + tid) * 2;
+                    float4 v;
+                    if (i + 1 < n) {
+                        v = __ldcs(reinterpret_cast<const float4 *>(pts) + i / 2);
+                    } else {
+                        const float2 a = reinterpret_cast<const float2 *>(pts)[i];
+                        v = make_float4(a.x, a.y, 0.0f, 0.0f);
+                    }
+                    px[2 * r] = v.x;
+                    py[2 * r] = v.y;
+                    px[2 * r + 1] = v.z;
+                    py[2 * r + 1] = v.w;
+                }
+            } else {
+                px[r] = py[r] = 0.0f;
+                if ((keep >> r) & 1u) {
+                    const float2 v = reinterpret_cast<const float2 *>(pts)[base + r * kFiltThreads + tid];
+                    px[r] = v.x;
+                    py[r] = v.y;
+                }
+            }
+        }
+        row_counts<G>(keep, s_off);
+        __syncthreads();
+        if (threadIdx.x < 32) scan_rows_warp0<G>(s_off);
+        __syncthreads();
+        scatter_tile<G, KEYS>(keep, base, st >> 32, s_off, px, py, surv_idx, surv_pts, out_keys, out_pay);
+        __syncthreads();
+    }
+}
+
+template <class K>
+int occupancy(K kernel, int threads)
+{
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0);
+    return v > 0 ? v : 1;
+}
+
+template <int G, bool KEYS>
+cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
+                          float *surv_pts, uint32_t *surv_count, cudaStream_t st)
+{
+    static int per_sm = occupancy(filter_kernel<G, KEYS>, kFiltThreads);
+    const int64_t ntiles = ceil_div(n, kFiltTile);
+    int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, ntiles);
+    filter_kernel<G, KEYS><<<(unsigned)std::max<int64_t>(blocks, 1), kFiltThreads, 0, st>>>(
         pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
-    probe_after(CH_K_FILTER, st);
     return cudaGetLastError();
+}
+
+template <int G, bool KEYS>
+cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
+                            float *surv_pts, uint32_t *surv_count, cudaStream_t st)
+{
+    static int per_sm_c = occupancy(filter_count_kernel<G>, kFiltThreads);
+    static int per_sm_s = occupancy(filter_scatter_kernel<G, KEYS>, kFiltThreads);
+    const int64_t ntiles = ceil_div(n, kFiltTile);
+    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_c, ntiles));
+    const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_s, ntiles));
+    filter_count_kernel<G><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, n, KEYS ? 1 : 0, surv_count);
+    filter_scatter_kernel<G, KEYS><<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx,
+                                                                          reinterpret_cast<float2 *>(surv_pts));
+    return cudaGetLastError();
+}
+
+int g_filter_variant = 0;   // 0: two passes, 1: single pass with look-back
+
+template <int G, bool KEYS>
+cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
+                           float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant)
+{
+    probe_before(CH_K_FILTER, st);
+    const cudaError_t e = variant == 1
+                              ? launch_single<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st)
+                              : launch_two_pass<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st);
+    probe_after(CH_K_FILTER, st);
+    return e;
 }
 
 }  // namespace
 
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st)
+                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant)
 {
+    const int v = variant < 0 ? g_filter_variant : variant;
     const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
     if (keys_mode)
-        return vec ? launch_t<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st)
-                   : launch_t<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st);
-    return vec ? launch_t<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st)
-               : launch_t<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st);
+        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v)
+                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v);
+    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v)
+               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v);
 }
 
 }  // namespace ch
+
+extern "C" ch_status ch_filter_variant(int32_t variant)
+{
+    if (variant != 0 && variant != 1) return CH_ERR_ARG;
+    ch::g_filter_variant = variant;
+    return CH_OK;
+}

@@ -22,10 +22,13 @@ cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout 
 cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, void *ws, const Layout &L,
                            unsigned long long *zero_ptr, int64_t zero_words, cudaStream_t st);
 
-// fused point test + stable compaction.  keys_mode: write (point key, index)
+// point test + stable compaction.  keys_mode: write (x key, (y key, index))
 // pairs into the sort buffers of ws instead of (index, point) outputs.
+// variant: 0 two passes (needs keep_bits in L), 1 single pass, -1 the
+// process-wide choice of ch_filter_variant.
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st);
+                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
+                          int variant = -1);
 
 // stable LSD radix sort of the survivor (key, index) pairs held in ws
 cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);

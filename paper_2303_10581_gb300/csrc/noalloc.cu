@@ -96,7 +96,8 @@ extern "C" ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32
     cudaError_t e = launch_octagon(pts, n, ext8, scratch, L, at<unsigned long long>(scratch, L.ctrl),
                                    (int64_t)L.zero_words, st);
     if (e != cudaSuccess) return CH_ERR_CUDA;
-    return launch_filter(pts, n, scratch, L, surv_idx, surv_pts, surv_count, false, st) == cudaSuccess
+    // the single-pass schedule: its only scratch is the look-back status
+    return launch_filter(pts, n, scratch, L, surv_idx, surv_pts, surv_count, false, st, 1) == cudaSuccess
                ? CH_OK
                : CH_ERR_CUDA;
 }

@@ -185,3 +185,19 @@ def test_out_of_range_extreme_index_is_an_argument_error():
     idx, sp, cnt = ch.filter_points(dev(p), ext, ws)
     assert ch.ch_last_error(ws.buf) == ch.CH_ERR_ARG
     assert int(cnt.item()) == 0
+
+
+@pytest.mark.parametrize("dist", pointgen.DISTRIBUTIONS)
+@pytest.mark.parametrize("n", [4095, 100_003, (1 << 20) + 7])
+def test_parity_single_pass_variant(dist, n):
+    """The single-pass look-back compaction gives the same lists."""
+    ch.ch_filter_variant(1)
+    try:
+        check_against_oracle(pointgen.make_points(dist, n, seed=2000 + n))
+    finally:
+        ch.ch_filter_variant(0)
+
+
+def test_filter_variant_rejects_unknown():
+    with pytest.raises(ch.CHError):
+        ch.ch_filter_variant(7)
