@@ -57,6 +57,8 @@ constexpr int LT = kChainThreads;   // leaves per super-chunk
 constexpr int SC = kChainC;         // points per super-chunk
 constexpr int CS = kChainStride;    // chain slots per super-chunk
 constexpr int NL = SC + 2;          // sequence capacity: SC points + 2 look-ahead slots
+constexpr int NWB = LT / 32;        // warps per block
+constexpr int LWMAX = ((NL + NWB - 1) / NWB + 31) / 32;   // longest leaf (17)
 
 // pop / advance test: lower chains drop a vertex when the turn is not
 // strictly counter-clockwise, upper chains when it is not strictly clockwise
@@ -131,7 +133,8 @@ __device__ void merge_walk(Acc &A, int side, int fa, int la, int fb, int lb)
 struct ChainSmem {
     float2 pts[NL];               // staged points; [SC], [SC+1]: look-ahead lowest / highest
     uint16_t list[3][NL];         // run starts, sequences and elimination ping-pong
-    uint8_t stk[LC * LT];         // leaf stacks: entry j of leaf t at [j * LT + t]
+    uint8_t stk[LWMAX * LT];      // leaf stacks: entry j of leaf t at [j * LT + t]
+    int16_t lb[LT];               // leaf t's first entry in the flat list array
     int16_t lo[LT], hi[LT], prv[LT], nxt[LT], first[LT], last[LT];
     uint32_t wsum[LT / 32];
     uint32_t total;
@@ -143,11 +146,10 @@ struct ChainSmem {
     int seq_len;
 };
 
-// leaf c covers sequence positions [c * LC, c * LC + LC); its stack holds
-// offsets into that range
+// leaf c's entries start at flat[lb[c]]; its stack holds offsets from there
 struct SmemAcc {
     ChainSmem &s;
-    const uint16_t *lst;
+    const uint16_t *flat;
     __device__ int lo(int, int c) const { return s.lo[c]; }
     __device__ int hi(int, int c) const { return s.hi[c]; }
     __device__ int prv(int, int c) const { return s.prv[c]; }
@@ -164,7 +166,7 @@ struct SmemAcc {
         s.nxt[a] = (int16_t)b;
         s.prv[b] = (int16_t)a;
     }
-    __device__ float2 point(int, int c, int k) const { return s.pts[lst[c * LC + s.stk[k * LT + c]]]; }
+    __device__ float2 point(int, int c, int k) const { return s.pts[flat[s.lb[c] + s.stk[k * LT + c]]]; }
 };
 
 // Exclusive scan of one count per thread over the block; the total goes to
@@ -418,7 +420,8 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     const int64_t nsc = ceil_div((int64_t)s, SC);
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const float kInf = __int_as_float(0x7f800000);
 
     for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
@@ -536,34 +539,47 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
                 }
             }
             __syncthreads();
-            int len = sm.seq_len;
-            // ---- elimination passes: keep the ends and the strict turns
-            int cur = 0;
-            for (int pass = 0; pass < kElimPasses && len > 2; ++pass) {
-                const uint16_t *src = sm.list[cur];
-                const int n_old = len;
-                len = block_compact(
-                    sm, n_old,
-                    [&](int j) {
-                        if (j == 0 || j == n_old - 1) return true;
-                        return !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
-                    },
-                    [&](int j) { return src[j]; }, sm.list[cur == 0 ? 2 : 0]);
-                cur = cur == 0 ? 2 : 0;
-                if (len == n_old) break;
+            const int len = sm.seq_len;
+            // ---- per warp: its share of the sequence, [warp * S, warp * S + S)
+            const int S = (len + NWB - 1) / NWB;
+            const int w0 = warp * S;
+            int wl = max(0, min(S, len - w0));   // this warp's live length
+            uint16_t *flat = &sm.list[0][0];
+            int cur = 0;                          // 0: list[0], 2: list[2]
+            // elimination passes over the warp's segment; its two ends stay
+            for (int pass = 0; pass < kElimPasses && wl > 2; ++pass) {
+                const uint16_t *src = flat + cur * NL + w0;
+                uint16_t *dst = flat + (2 - cur) * NL + w0;
+                int kept = 0;
+                for (int c0 = 0; c0 < wl; c0 += 32) {
+                    const int j = c0 + lane;
+                    bool k = false;
+                    if (j < wl)
+                        k = j == 0 || j == wl - 1 ||
+                            !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
+                    const uint32_t m = __ballot_sync(0xffffffffu, k);
+                    if (k) dst[kept + __popc(m & lt)] = src[j];
+                    kept += __popc(m);
+                }
+                __syncwarp();
+                cur = 2 - cur;
+                const bool done = kept == wl;
+                wl = kept;
+                if (done) break;
             }
-            const uint16_t *lst = sm.list[cur];
-
-            // ---- leaf chain over sequence positions [t * LC, t * LC + cnt)
-            const int cnt = max(0, min(LC, len - t * LC));
+            // ---- leaf chains: lane l takes [l * LW, l * LW + LW) of the warp's list
+            const int LW = (wl + 31) / 32;
+            const int lbase = cur * NL + w0 + lane * LW;
+            const int cnt = max(0, min(LW, wl - lane * LW));
+            sm.lb[t] = (int16_t)lbase;
             int h = 0;
             float2 t1 = make_float2(0.0f, 0.0f), t2 = t1;   // top and second of the stack
             for (int k = 0; k < cnt; ++k) {
-                const float2 p = sm.pts[lst[t * LC + k]];
+                const float2 p = sm.pts[flat[lbase + k]];
                 while (h >= 2 && drop(side, t2, t1, p)) {
                     --h;
                     t1 = t2;
-                    if (h >= 2) t2 = sm.pts[lst[t * LC + sm.stk[(h - 2) * LT + t]]];
+                    if (h >= 2) t2 = sm.pts[flat[lbase + sm.stk[(h - 2) * LT + t]]];
                 }
                 sm.stk[h * LT + t] = (uint8_t)k;
                 ++h;
@@ -573,11 +589,22 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
             sm.lo[t] = 0;
             sm.hi[t] = (int16_t)(h - 1);
             sm.first[t] = sm.last[t] = (int16_t)(h > 0 ? t : -1);
+            __syncwarp();
+            // ---- merge tree: five levels inside the warp, then three across warps
+            SmemAcc A{sm, flat};
+            for (int w = 1; w < 32; w *= 2) {
+                if (lane < 32 / (2 * w)) {
+                    const int a0 = warp * 32 + 2 * lane * w, b0 = a0 + w;
+                    const int fa = sm.first[a0], la = sm.last[a0];
+                    const int fb = sm.first[b0], lb = sm.last[b0];
+                    if (la >= 0 && fb >= 0) merge_walk(A, side, fa, la, fb, lb);
+                    sm.first[a0] = (int16_t)(la >= 0 ? fa : fb);
+                    sm.last[a0] = (int16_t)(fb >= 0 ? lb : la);
+                }
+                __syncwarp();
+            }
             __syncthreads();
-
-            // ---- in-block merge tree over the leaves
-            SmemAcc A{sm, lst};
-            for (int w = 1; w < LT; w *= 2) {
+            for (int w = 32; w < LT; w *= 2) {
                 if (t < LT / (2 * w)) {
                     const int a0 = 2 * t * w, b0 = a0 + w;
                     const int fa = sm.first[a0], la = sm.last[a0];
@@ -596,7 +623,7 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
             uint32_t *dpos = P.pos[side] + sc * CS + off;
             float2 *dpt = P.pt[side] + sc * CS + off;
             for (int q = 0; q < c; ++q) {
-                const int e = lst[t * LC + sm.stk[(l + q) * LT + t]];
+                const int e = flat[lbase + sm.stk[(l + q) * LT + t]];
                 dpos[q] = e < SC ? (uint32_t)(base + e) : sm.ext_pos[e - SC];
                 dpt[q] = sm.pts[e];
             }
