@@ -235,3 +235,21 @@ def convex_hull(pts, ws: Workspace | None = None):
     cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
     ch_hull(pts, idx, cnt, ws.buf)
     return idx, cnt
+
+
+def convex_hull_batched(pts, offsets, ws: Workspace | None = None):
+    """(hull_idx, hull_offsets) on the device for the sets
+    pts[offsets[b]:offsets[b+1]]; set b's hull (set-local indices) is
+    hull_idx[hull_offsets[b]:hull_offsets[b+1]]."""
+    import torch
+    pts = _as_points(pts)
+    n = pts.shape[0]
+    if offsets.dtype != torch.int64 or offsets.dim() != 1 or offsets.shape[0] < 1:
+        raise ValueError("offsets must be a 1-d int64 tensor of num_sets + 1 entries")
+    offsets = offsets.to(pts.device).contiguous()
+    num_sets = offsets.shape[0] - 1
+    ws = ws or Workspace(n, num_sets=max(num_sets, 1), device=pts.device)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+    hoff = torch.zeros(num_sets + 1, dtype=torch.int64, device=pts.device)
+    ch_hull_batched(pts, offsets, idx, hoff, ws.buf)
+    return idx, hoff

@@ -2,6 +2,7 @@
 // Host code only: argument checks, workspace layout, launches.  No
 // allocation, no host synchronisation (except ch_last_error), no host
 // fallback: every step of Algorithm 1 runs in the kernels of this library.
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -24,13 +25,17 @@ inline ch_status check_ws(void *ws, size_t ws_bytes, const Layout &L)
 
 inline ch_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CH_OK : CH_ERR_CUDA; }
 
+// Workspace bytes of a batched call over n points in B sets.
+size_t batched_bytes(int64_t n, int64_t B) { return make_batch_layout(make_layout(n, B), B).total; }
+
 }  // namespace
 
 extern "C" ch_status ch_workspace_size(int64_t n, int64_t num_sets, size_t *bytes)
 {
     if (!bytes || n < 0 || num_sets < 1) return CH_ERR_ARG;
     if (n > kMaxN) return CH_ERR_CAPACITY;
-    *bytes = make_layout(n).total;
+    // the batched layout holds the single-set one as a prefix
+    *bytes = batched_bytes(n, num_sets);
     return CH_OK;
 }
 
@@ -89,15 +94,34 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
 extern "C" ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_sets, uint32_t *hull_idx,
                                      int64_t *hull_offsets, void *ws, size_t ws_bytes, void *stream)
 {
-    (void)pts;
-    (void)offsets;
-    (void)num_sets;
-    (void)hull_idx;
-    (void)hull_offsets;
-    (void)ws;
-    (void)ws_bytes;
-    (void)stream;
-    return CH_ERR_UNSUPPORTED;
+    if (num_sets < 0 || !offsets || !hull_offsets || !aligned(offsets, 8) || !aligned(hull_offsets, 8))
+        return CH_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    if (num_sets == 0) return cuda_status(cudaMemsetAsync(hull_offsets, 0, sizeof(int64_t), st));
+    if (!pts || !hull_idx || !aligned(pts, 8) || !aligned(hull_idx, 4)) return CH_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return CH_ERR_ARG;
+    // The total point count offsets[num_sets] is only known on the device:
+    // the layout is built for the most points the workspace can hold, and
+    // the device checks the offsets against that capacity.
+    if (ws_bytes < batched_bytes(0, num_sets)) return CH_ERR_CAPACITY;
+    int64_t lo = 0, hi = kMaxHullN - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (batched_bytes(mid, num_sets) <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t n_cap = lo;
+    const Layout L = make_layout(std::max<int64_t>(n_cap, 1), num_sets);
+    const BatchLayout BL = make_batch_layout(L, num_sets);
+    cudaError_t e = cudaMemsetAsync(at<char>(ws, L.ctrl), 0, L.zero_words * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(ws, BL.zero_begin), 0, BL.zero_end - BL.zero_begin, st);
+    if (e == cudaSuccess) e = launch_bx_setup(offsets, ws, L, BL, n_cap, st);
+    if (e == cudaSuccess) e = launch_bx_extremes(pts, ws, L, BL, st);
+    if (e == cudaSuccess) e = launch_bx_filter(pts, ws, L, BL, st);
+    if (e == cudaSuccess) e = launch_bx_sort(ws, L, BL, st);
+    if (e == cudaSuccess) e = launch_bx_chain(ws, L, BL, st);
+    if (e == cudaSuccess) e = launch_bx_finish(ws, L, BL, hull_idx, hull_offsets, st);
+    return cuda_status(e);
 }
 
 extern "C" ch_status ch_last_error(void *ws, void *stream)

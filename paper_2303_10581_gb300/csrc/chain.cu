@@ -304,22 +304,25 @@ struct GlobalAcc {
     __device__ float2 point(int side, int c, int k) const { return __ldcg(P.pt[side] + (int64_t)c * CS + k); }
 };
 
-// first / last live super-chunk of tree node (level, j); level 0 = super-chunk j
-__device__ __forceinline__ void node_ends(const ChainPtrs &P, int level, int64_t nb, int64_t j, int side,
-                                          int32_t &first, int32_t &last)
+// first / last live super-chunk (absolute index) of tree node (level, j)
+// of a tree whose leaves are super-chunks coff + 0 .. and whose nodes start
+// at node noff; level 0 = super-chunk coff + j
+__device__ __forceinline__ void node_ends(const ChainPtrs &P, int level, int64_t coff, int64_t noff, int64_t nb,
+                                          int64_t j, int side, int32_t &first, int32_t &last)
 {
     if (level == 0) {
-        const bool live = __ldcg(P.hi[side] + j) >= __ldcg(P.lo[side] + j);
-        first = last = live ? (int32_t)j : -1;
+        const bool live = __ldcg(P.hi[side] + coff + j) >= __ldcg(P.lo[side] + coff + j);
+        first = last = live ? (int32_t)(coff + j) : -1;
     } else {
-        first = __ldcg(P.node + (nb + j) * 4 + 2 * side);
-        last = __ldcg(P.node + (nb + j) * 4 + 2 * side + 1);
+        first = __ldcg(P.node + (noff + nb + j) * 4 + 2 * side);
+        last = __ldcg(P.node + (noff + nb + j) * 4 + 2 * side + 1);
     }
 }
 
-// Climb the global tree from super-chunk c: the second child to arrive at a
-// node merges its two children and continues upward.
-__device__ void climb(const ChainPtrs &P, int64_t c, int64_t nsc)
+// Climb the merge tree of one set from its super-chunk c (0 <= c < nsc;
+// leaves at coff, nodes at noff): the second child to arrive at a node
+// merges its two children and continues upward.
+__device__ void climb(const ChainPtrs &P, int64_t c, int64_t nsc, int64_t coff, int64_t noff)
 {
     GlobalAcc G{P};
     int64_t node = c, w = nsc, nb_child = 0, nb = 0;   // nb: base of the level above
@@ -331,17 +334,17 @@ __device__ void climb(const ChainPtrs &P, int64_t c, int64_t nsc)
         if (sib >= w) {
 #pragma unroll
             for (int side = 0; side < 2; ++side)
-                node_ends(P, level, nb_child, node, side, rec[2 * side], rec[2 * side + 1]);
+                node_ends(P, level, coff, noff, nb_child, node, side, rec[2 * side], rec[2 * side + 1]);
         } else {
             __threadfence();
-            if (atomicAdd(P.node_cnt + nb + parent, 1) == 0) return;   // first to arrive: the sibling merges
+            if (atomicAdd(P.node_cnt + noff + nb + parent, 1) == 0) return;   // first to arrive: the sibling merges
             __threadfence();
             const int64_t a = parent * 2, b = a + 1;
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 int32_t fa, la, fb, lb;
-                node_ends(P, level, nb_child, a, side, fa, la);
-                node_ends(P, level, nb_child, b, side, fb, lb);
+                node_ends(P, level, coff, noff, nb_child, a, side, fa, la);
+                node_ends(P, level, coff, noff, nb_child, b, side, fb, lb);
                 if (la < 0) {
                     rec[2 * side] = fb;
                     rec[2 * side + 1] = lb;
@@ -356,7 +359,7 @@ __device__ void climb(const ChainPtrs &P, int64_t c, int64_t nsc)
             }
         }
 #pragma unroll
-        for (int f = 0; f < 4; ++f) P.node[(nb + parent) * 4 + f] = rec[f];
+        for (int f = 0; f < 4; ++f) P.node[(noff + nb + parent) * 4 + f] = rec[f];
         node = parent;
         nb_child = nb;
         nb += pw;
@@ -410,28 +413,22 @@ __device__ __forceinline__ void block_extreme_y(ChainSmem &s, float ylo, uint32_
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
+// The chains of one super-chunk: sorted positions [base, base + m) of a set
+// occupying [sbeg, send); results go to chain slot j.  Called by all
+// threads of the block.
+__device__ void superchunk(ChainSmem &sm, const ChainPtrs &P, int64_t j, int64_t base, int m, int64_t sbeg,
+                           int64_t send)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
-    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
-    if (s == 0) return;
-    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
-    const int64_t nsc = ceil_div((int64_t)s, SC);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const float kInf = __int_as_float(0x7f800000);
-
-    for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
-        const int64_t base = sc * SC;
-        const int m = (int)min((int64_t)SC, (int64_t)s - base);
+    const int64_t sc = j;
+    {
         // ---- stage the super-chunk (coalesced), decoded to points
         for (int i = t; i < m; i += LT) sm.pts[i] = sorted_point(P, base + i);
         if (t == 0) {
-            sm.has_prev = base > 0;
-            sm.prev_x = base > 0 ? key_float(__ldg(P.keys + base - 1)) : 0.0f;
+            sm.has_prev = base > sbeg;
+            sm.prev_x = base > sbeg ? key_float(__ldg(P.keys + base - 1)) : 0.0f;
         }
         __syncthreads();
 
@@ -449,18 +446,18 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
                     P.hi[side][sc] = -1;
                 }
             __syncthreads();
-            continue;
+            return;
         }
         // ---- look ahead when the last run continues past the super-chunk
         const float xr = sm.pts[m - 1].x;
-        const bool ext = base + m < (int64_t)s && key_float(__ldg(P.keys + base + m)) == xr;
+        const bool ext = base + m < send && key_float(__ldg(P.keys + base + m)) == xr;
         int64_t run_end = base + m;
         if (ext) {
             float ylo = kInf, yhi = -kInf;
             uint32_t qlo = 0xffffffffu, qhi = 0xffffffffu;
             for (int64_t q0 = base + m;; q0 += LT) {
                 const int64_t q = q0 + t;
-                const bool in_run = q < (int64_t)s && key_float(__ldg(P.keys + q)) == xr;
+                const bool in_run = q < send && key_float(__ldg(P.keys + q)) == xr;
                 if (in_run) {
                     const float y = key_float((uint32_t)(__ldg(P.pay + q) >> 32));
                     if (y < ylo || (y == ylo && (uint32_t)q < qlo)) {
@@ -489,7 +486,7 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
                 sm.ext_pos[1] = oqh;
             }
         }
-        const bool holds_last = run_end == (int64_t)s;
+        const bool holds_last = run_end == send;
         __syncthreads();
         // ---- representatives: lowest (list[0]) and highest (list[1]) point of each run
         for (int k = t; k < R; k += LT) {
@@ -517,7 +514,7 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
         }
         __syncthreads();
         const uint16_t first_lo = sm.list[0][0];
-        const bool first_two = base == 0 && sm.pts[sm.list[1][0]].y > sm.pts[first_lo].y;
+        const bool first_two = base == sbeg && sm.pts[sm.list[1][0]].y > sm.pts[first_lo].y;
 
         for (int side = 0; side < 2; ++side) {
             // ---- this side's sequence in list[0]
@@ -636,6 +633,20 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
     }
 }
 
+__global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    if (s == 0) return;
+    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
+    const int64_t nsc = ceil_div((int64_t)s, SC);
+    for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x)
+        superchunk(sm, P, sc, sc * SC, (int)min((int64_t)SC, (int64_t)s - sc * SC), 0, s);
+}
+
 // Global merge tree over the super-chunks: one thread per super-chunk
 // climbs; the second child to reach a node merges the pair.
 __global__ void __launch_bounds__(32) chain_merge_kernel(void *ws, Layout L)
@@ -647,22 +658,57 @@ __global__ void __launch_bounds__(32) chain_merge_kernel(void *ws, Layout L)
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     const int64_t nsc = ceil_div((int64_t)s, SC);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < nsc) climb(P, c, nsc);
+    if (c < nsc) climb(P, c, nsc, 0, 0);
 }
 
-// Compacts the live chain ranges: thread = super-chunk, look-back over
-// tiles of super-chunks, warp-cooperative copies.  Side 0 goes to
-// hull_idx, side 1 to utmp.
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, uint32_t *hull_idx)
+// ---- many sets: super-chunks never span two sets; each set has its own
+// merge tree; the sorted arrays end up in buffer 0 (four passes)
+__global__ void __launch_bounds__(LT) bx_chain_kernel(void *ws, Layout L, BatchLayout BL)
 {
-    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
-    if (s == 0) return;
-    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
-    const int64_t nc = ceil_div((int64_t)s, SC);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *sc_set = at<uint32_t>(ws, BL.sc_set);
+    const ChainPtrs P = chain_ptrs(ws, L, 0);
+    const int64_t nsc = bc->nsc;
+    for (int64_t j = blockIdx.x; j < nsc; j += gridDim.x) {
+        const uint32_t b = sc_set[j];
+        const int64_t sb = (int64_t)sets[b].surv_base, n = sets[b].s;
+        const int64_t local = j - sets[b].sc_base;
+        superchunk(sm, P, j, sb + local * SC, (int)min((int64_t)SC, n - local * SC), sb, sb + n);
+    }
+}
+
+__global__ void __launch_bounds__(32) bx_merge_kernel(void *ws, Layout L, BatchLayout BL)
+{
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *sc_set = at<uint32_t>(ws, BL.sc_set);
+    const ChainPtrs P = chain_ptrs(ws, L, 0);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (int64_t)bc->nsc) return;
+    const uint32_t b = sc_set[j];
+    climb(P, j - sets[b].sc_base, sets[b].nsc, sets[b].sc_base, sets[b].node_base);
+}
+
+// Compacts the live chain ranges of super-chunks [0, nc): thread =
+// super-chunk, look-back over tiles of super-chunks, warp-cooperative
+// copies of the original indices (low half of the payload).  Side 0 goes to
+// out0, side 1 to out1.  With sc_off, each super-chunk's output offset per
+// side is recorded too (sc_off[side][nc] = side total).
+struct EmitArgs {
+    uint32_t *out[2];
+    uint32_t *sc_off[2];
+    uint32_t *ticket;
+    uint32_t *h_total[2];
+};
+
+__device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t nc, uint64_t s, const EmitArgs &E)
+{
     const int64_t ntiles = ceil_div(nc, kEmitThreads);
-    uint32_t *utmp = at<uint32_t>(ws, L.utmp);
     unsigned long long *status[2] = {at<unsigned long long>(ws, L.emit_status[0]),
                                      at<unsigned long long>(ws, L.emit_status[1])};
     constexpr int NW = kEmitThreads / 32;
@@ -671,7 +717,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
     __shared__ unsigned long long s_excl[2];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(&ctrl->emit_ticket[0], 1u);
+        if (tid == 0) s_tile = atomicAdd(E.ticket, 1u);
         __syncthreads();
         const int64_t tile = s_tile;
         if (tile >= ntiles) break;
@@ -720,8 +766,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
             if (lane == 0) {
                 s_excl[side] = excl;
                 if (tile == ntiles - 1) {
-                    if (side == 0) ctrl->h_lower = (uint32_t)(excl + total);
-                    else ctrl->h_upper = (uint32_t)(excl + total);
+                    *E.h_total[side] = (uint32_t)(excl + total);
+                    if (E.sc_off[side]) E.sc_off[side][nc] = (uint32_t)(excl + total);
                 }
             }
         }
@@ -729,7 +775,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const uint64_t mypos = s_excl[side] + s_wsum[side][warp] + pre[side];
-            uint32_t *out = side == 0 ? hull_idx : utmp;
+            if (E.sc_off[side] && c < nc) E.sc_off[side][c] = (uint32_t)mypos;
+            uint32_t *out = E.out[side];
             const uint32_t *chain = P.pos[side];
             for (int i = 0; i < 32; ++i) {
                 const int32_t n_i = __shfl_sync(0xffffffffu, cnt[side], i);
@@ -745,6 +792,34 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, uint32_t *hull_idx)
+{
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    if (s == 0) return;
+    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
+    EmitArgs E{{hull_idx, at<uint32_t>(ws, L.utmp)}, {nullptr, nullptr}, &ctrl->emit_ticket[0],
+               {&ctrl->h_lower, &ctrl->h_upper}};
+    emit_body(ws, L, P, ceil_div((int64_t)s, SC), s, E);
+}
+
+// all sets at once: lower chains to the batch's lower array, upper chains
+// to utmp, each set's part delimited by the per-super-chunk offsets
+__global__ void __launch_bounds__(kEmitThreads) bx_emit_kernel(void *ws, Layout L, BatchLayout BL)
+{
+    BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const int64_t nc = bc->nsc;
+    if (nc == 0) return;
+    const ChainPtrs P = chain_ptrs(ws, L, 0);
+    EmitArgs E{{at<uint32_t>(ws, BL.lower), at<uint32_t>(ws, L.utmp)},
+               {at<uint32_t>(ws, BL.sc_off[0]), at<uint32_t>(ws, BL.sc_off[1])},
+               &bc->emit_ticket,
+               {&bc->h_lower, &bc->h_upper}};
+    emit_body(ws, L, P, nc, (uint64_t)L.n, E);
 }
 
 // hull = lower chain, then the upper chain reversed without its two ends
@@ -795,6 +870,34 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
     probe_before(CH_K_FINISH, st);
     finish_kernel<<<(unsigned)fb, 256, 0, st>>>(ws, L, hull_idx, hull_count);
     probe_after(CH_K_FINISH, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
+{
+    const int sms = sm_count();
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(bx_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChainSmem));
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, bx_chain_kernel, LT, sizeof(ChainSmem));
+        per_sm = v > 0 ? v : 1;
+    }
+    int64_t cb = BL.tiles_max;
+    if (cb > (int64_t)sms * per_sm) cb = (int64_t)sms * per_sm;
+    if (cb < 1) cb = 1;
+    probe_before(CH_K_CHAIN, st);
+    bx_chain_kernel<<<(unsigned)cb, LT, sizeof(ChainSmem), st>>>(ws, L, BL);
+    bx_merge_kernel<<<(unsigned)ceil_div(BL.tiles_max, 32), 32, 0, st>>>(ws, L, BL);
+    probe_after(CH_K_CHAIN, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t eb = ceil_div(BL.tiles_max, kEmitThreads);
+    if (eb > (int64_t)sms * 4) eb = (int64_t)sms * 4;
+    if (eb < 1) eb = 1;
+    probe_before(CH_K_EMIT, st);
+    bx_emit_kernel<<<(unsigned)eb, kEmitThreads, 0, st>>>(ws, L, BL);
+    probe_after(CH_K_EMIT, st);
     return cudaGetLastError();
 }
 

@@ -133,7 +133,51 @@ __host__ __device__ inline int64_t tree_nodes(int64_t nc)
     return total;
 }
 
-__host__ __device__ inline Layout make_layout(int64_t n)
+// Per-set bookkeeping of ch_hull_batched (all positions are global).
+struct SetInfo {
+    int64_t pt_begin;     // first point of the set in pts
+    int64_t n;            // points in the set
+    uint32_t tile_base;   // first 4096-point tile of the set
+    uint32_t ntiles;
+    uint32_t s;           // survivors of the filter
+    uint32_t sc_base;     // first 4096-survivor super-chunk (= sort tile) of the set
+    uint64_t surv_base;   // first survivor of the set in the sort arrays
+    uint32_t nsc;         // super-chunks of the set
+    uint32_t node_base;   // first merge-tree node of the set
+    uint32_t hull;        // hull vertices of the set
+    uint32_t pad[3];
+};
+
+// Batch-wide counters of ch_hull_batched (zeroed at the start of a call).
+struct BatchCtrl {
+    uint32_t tiles;       // point tiles over all sets
+    uint32_t nsc;         // super-chunks over all sets
+    uint32_t abort;       // bad offsets: nothing is computed
+    uint32_t filt_ticket, emit_ticket, pad0;
+    uint32_t sort_ticket[kSortPasses];
+    uint32_t h_lower, h_upper;
+    uint32_t pad[4];
+};
+
+// Extra workspace of ch_hull_batched, after the single-set regions.
+struct BatchLayout {
+    size_t sets;          // SetInfo[B]
+    size_t octs;          // Octagon[B]
+    size_t zero_begin;    // ---- zeroed by one memset per call:
+    size_t bctrl;         // BatchCtrl
+    size_t ext_slot;      // u64[B * 8]: packed extremes per set
+    size_t nonfinite;     // u32[B]
+    size_t hist;          // u32[B * kSortPasses * 256]
+    size_t zero_end;      // ----
+    size_t tile_set;      // u32[tiles_max]: set of each point tile
+    size_t sc_set;        // u32[tiles_max]: set of each super-chunk
+    size_t sc_off[2];     // u32[tiles_max + 1]: lower / upper chain offset of each super-chunk
+    size_t lower;         // u32[n]: lower chains of all sets (set-local indices); aliases keys[1]
+    size_t total;
+    int64_t num_sets, tiles_max;
+};
+
+__host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
 {
     Layout L{};
     if (n < 1) n = 1;
@@ -142,6 +186,12 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     L.sort_tiles = ceil_div(n, kSortTile);
     L.n_chunks = ceil_div(n, kChainC);
     L.n_nodes = tree_nodes(L.n_chunks) + 1;
+    if (sets > 0) {
+        // every set adds at most one ragged tile / super-chunk, and each
+        // set's merge tree has fewer than twice as many nodes as leaves
+        L.filt_tiles = L.sort_tiles = L.n_chunks = ceil_div(n, kChainC) + sets;
+        L.n_nodes = 2 * L.n_chunks + sets;
+    }
     L.emit_tiles = ceil_div(L.n_chunks, kEmitThreads);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -175,6 +225,34 @@ __host__ __device__ inline Layout make_layout(int64_t n)
     L.utmp = take((size_t)n * 4);
     L.total = o;
     return L;
+}
+
+__host__ __device__ inline BatchLayout make_batch_layout(const Layout &L, int64_t sets)
+{
+    BatchLayout B{};
+    B.num_sets = sets;
+    B.tiles_max = L.n_chunks;
+    size_t o = L.total;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    B.sets = take((size_t)sets * sizeof(SetInfo));
+    B.octs = take((size_t)sets * sizeof(Octagon));
+    B.zero_begin = o;
+    B.bctrl = take(sizeof(BatchCtrl));
+    B.ext_slot = take((size_t)sets * 8 * 8);
+    B.nonfinite = take((size_t)sets * 4);
+    B.hist = take((size_t)sets * kSortPasses * 256 * 4);
+    B.zero_end = o;
+    B.tile_set = take((size_t)B.tiles_max * 4);
+    B.sc_set = take((size_t)B.tiles_max * 4);
+    B.sc_off[0] = take((size_t)(B.tiles_max + 1) * 4);
+    B.sc_off[1] = take((size_t)(B.tiles_max + 1) * 4);
+    B.lower = L.keys[1];   // the second sort buffer is free once the sort ends in buffer 0
+    B.total = o;
+    return B;
 }
 
 template <class T>

@@ -13,6 +13,8 @@
 // one 64-bit atomicMax per slot on (order-preserving key << 32 | ~index),
 // which selects the largest key and, among equal keys, the lowest index.
 // The last block to finish decodes the winners and builds the polygon.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -308,6 +310,112 @@ __global__ void octagon_kernel(const float *__restrict__ pts, int64_t n, const u
         __syncwarp();
         build_octagon_warp(reinterpret_cast<const float2 *>(pts), s_ext, oct);
     }
+}
+
+// ---------------------------------------------------------------------------
+// many sets (ch_hull_batched): the same reduction per 4096-point tile of one
+// set, finished with per-set packed atomics; then one warp per set builds
+// its polygon.  Indices are set-local.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                          BatchLayout BL)
+{
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *tile_set = at<uint32_t>(ws, BL.tile_set);
+    unsigned long long *slots = at<unsigned long long>(ws, BL.ext_slot);
+    uint32_t *nonfin = at<uint32_t>(ws, BL.nonfinite);
+    __shared__ float sk[8][8];
+    __shared__ uint32_t si_[8][8];
+    __shared__ int s_bad;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t T = bc->tiles;
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const uint32_t b = tile_set[t];
+        const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
+        const int64_t hi = min(lo + kFiltTile, sets[b].n);
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin;
+        Best best;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            best.k[j] = __int_as_float(0x7fc00000);
+            best.i[j] = 0xffffffffu;
+        }
+        float nf = 0.0f;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float2 v = __ldcs(p2 + i);
+            nf = __fmaf_rn(v.x, 0.0f, __fmaf_rn(v.y, 0.0f, nf));
+            consider(best, v.x, v.y, (uint32_t)i);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float ok = __shfl_xor_sync(0xffffffffu, best.k[j], o);
+                const uint32_t oi = __shfl_xor_sync(0xffffffffu, best.i[j], o);
+                combine(best.k[j], best.i[j], ok, oi);
+            }
+        }
+        if (threadIdx.x == 0) s_bad = 0;
+        __syncthreads();
+        if (nf != nf) s_bad = 1;
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                sk[warp][j] = best.k[j];
+                si_[warp][j] = best.i[j];
+            }
+        __syncthreads();
+        if (warp == 0 && lane < 8) {
+            float k = sk[0][lane];
+            uint32_t i = si_[0][lane];
+            for (int w = 1; w < 8; ++w) combine(k, i, sk[w][lane], si_[w][lane]);
+            if (i != 0xffffffffu)
+                atomicMax(&slots[(size_t)b * 8 + lane], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
+            if (lane == 0 && s_bad) atomicOr(&nonfin[b], 1u);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) bx_octagon_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                         BatchLayout BL)
+{
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const unsigned long long *slots = at<unsigned long long>(ws, BL.ext_slot);
+    const uint32_t *nonfin = at<uint32_t>(ws, BL.nonfinite);
+    Octagon *octs = at<Octagon>(ws, BL.octs);
+    __shared__ uint32_t s_ext[8][8];
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const int64_t b = (int64_t)blockIdx.x * 8 + warp;
+    if (b >= BL.num_sets) return;
+    Octagon *out = octs + b;
+    if (bc->abort || sets[b].n == 0) {   // nothing to do: empty hull
+        if (lane == 0) out->abort = 1;
+        return;
+    }
+    if (nonfin[b]) {
+        if (lane == 0) {
+            out->abort = 1;
+            set_error(ws, L, kErrNonFinite, 3);
+        }
+        return;
+    }
+    if (lane < 8) s_ext[warp][lane] = ~(uint32_t)slots[b * 8 + lane];
+    __syncwarp();
+    build_octagon_warp(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, s_ext[warp], out);
+}
+
+cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
+{
+    int64_t blocks = std::min<int64_t>(BL.tiles_max, (int64_t)sm_count() * 8);
+    probe_before(CH_K_EXTREMES, st);
+    bx_extremes_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(pts, ws, L, BL);
+    bx_octagon_kernel<<<(unsigned)ceil_div(BL.num_sets, 8), 256, 0, st>>>(pts, ws, L, BL);
+    probe_after(CH_K_EXTREMES, st);
+    return cudaGetLastError();
 }
 
 int sm_count()

@@ -413,6 +413,218 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
     }
 }
 
+// ---------------------------------------------------------------------------
+// many sets (ch_hull_batched): the two passes over set-aligned 4096-point
+// tiles, with 8-byte loads (sets start anywhere); indices are set-local
+// ---------------------------------------------------------------------------
+// Thread t tests points lo + r * 256 + t of the set (r < 16), below hi.
+__device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, int64_t lo, int64_t hi,
+                                                 const Octagon &so, float (&px)[kFiltItems],
+                                                 float (&py)[kFiltItems])
+{
+    uint32_t keep = 0;
+#pragma unroll
+    for (int r = 0; r < kFiltItems; ++r) {
+        const int64_t i = lo + r * kFiltThreads + threadIdx.x;
+        px[r] = py[r] = 0.0f;
+        if (i < hi) {
+            const float2 v = __ldcs(p2 + i);
+            px[r] = v.x;
+            py[r] = v.y;
+            if (keep_point(so, v.x, v.y)) keep |= 1u << r;
+        }
+    }
+    return keep;
+}
+
+// Copies set b's polygon to shared memory when the block moves to a new set.
+__device__ __forceinline__ void bx_octagon_to_smem(Octagon &so, int64_t &cur, int64_t b, const Octagon *octs)
+{
+    if (b == cur) return;   // block-uniform
+    __syncthreads();
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(octs + b);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&so);
+    for (uint32_t w = threadIdx.x; w < sizeof(Octagon) / 4; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    cur = b;
+}
+
+__global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const float *__restrict__ pts, void *ws,
+                                                                       Layout L, BatchLayout BL)
+{
+    __shared__ Octagon so;
+    __shared__ uint32_t s_w[NW];
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *tile_set = at<uint32_t>(ws, BL.tile_set);
+    const Octagon *octs = at<Octagon>(ws, BL.octs);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t T = bc->tiles;
+    int64_t cur = -1;
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const int64_t b = tile_set[t];
+        bx_octagon_to_smem(so, cur, b, octs);
+        uint32_t keep = 0;
+        if (!so.abort) {
+            const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
+            const int64_t hi = min(lo + kFiltTile, sets[b].n);
+            float px[kFiltItems], py[kFiltItems];
+            keep = bx_load_test(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, lo, hi, so, px, py);
+        }
+        bits[(size_t)t * kFiltThreads + threadIdx.x] = (uint16_t)keep;
+        uint32_t c = __popc(keep);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) s_w[warp] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sum += s_w[w];
+            status[t] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// One block: tile offsets (exclusive scan of the counts), each set's
+// survivor range, and the layout of the later stages: each set's
+// super-chunks (4096 survivors, also the sort tiles) and merge-tree nodes.
+__global__ void __launch_bounds__(1024) bx_filter_scan_kernel(void *ws, Layout L, BatchLayout BL)
+{
+    __shared__ uint64_t s_w[32];
+    __shared__ uint64_t s_w2[32];
+    __shared__ uint64_t s_total;
+    BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    uint32_t *sc_set = at<uint32_t>(ws, BL.sc_set);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nthr = blockDim.x;
+    // ---- 1. tiles
+    {
+        const int64_t T = bc->tiles;
+        const int64_t per = ceil_div(T, (int64_t)nthr);
+        const int64_t t0 = threadIdx.x * per, t1 = min(t0 + per, T);
+        uint64_t sum = 0;
+        for (int64_t t = t0; t < t1; ++t) sum += status[t] & 0xffffffffull;
+        uint64_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint64_t before = 0, total = 0;
+        for (uint32_t w = 0; w < nthr / 32; ++w) {
+            if (w < warp) before += s_w[w];
+            total += s_w[w];
+        }
+        uint64_t run = before + incl - sum;
+        for (int64_t t = t0; t < t1; ++t) {
+            const uint64_t c = status[t] & 0xffffffffull;
+            status[t] = (run << 32) | c;
+            run += c;
+        }
+        if (threadIdx.x == 0) s_total = total;
+        __syncthreads();
+    }
+    // ---- 2. sets: survivors, super-chunks, tree nodes
+    const int64_t B = BL.num_sets;
+    const int64_t T = bc->tiles;
+    const uint64_t total = s_total;
+    auto off = [&](int64_t t) -> uint64_t { return t < T ? (status[t] >> 32) : total; };
+    const int64_t per = ceil_div(B, (int64_t)nthr);
+    const int64_t b0 = threadIdx.x * per, b1 = min(b0 + per, B);
+    uint64_t sc_sum = 0, nd_sum = 0;
+    for (int64_t b = b0; b < b1; ++b) {
+        const uint64_t sb = off(sets[b].tile_base);
+        const uint32_t s = (uint32_t)(off(sets[b].tile_base + sets[b].ntiles) - sb);
+        sets[b].surv_base = sb;
+        sets[b].s = s;
+        const int64_t nsc = ceil_div((int64_t)s, kChainC);
+        sets[b].nsc = (uint32_t)nsc;
+        sc_sum += nsc;
+        nd_sum += nsc > 0 ? tree_nodes(nsc) + 1 : 0;
+    }
+    uint64_t i1 = sc_sum, i2 = nd_sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u1 = __shfl_up_sync(0xffffffffu, i1, o);
+        const uint64_t u2 = __shfl_up_sync(0xffffffffu, i2, o);
+        if (lane >= (uint32_t)o) {
+            i1 += u1;
+            i2 += u2;
+        }
+    }
+    __syncthreads();
+    if (lane == 31) {
+        s_w[warp] = i1;
+        s_w2[warp] = i2;
+    }
+    __syncthreads();
+    uint64_t bsc = 0, bnd = 0, tsc = 0;
+    for (uint32_t w = 0; w < nthr / 32; ++w) {
+        if (w < warp) {
+            bsc += s_w[w];
+            bnd += s_w2[w];
+        }
+        tsc += s_w[w];
+    }
+    uint64_t rsc = bsc + i1 - sc_sum, rnd = bnd + i2 - nd_sum;
+    for (int64_t b = b0; b < b1; ++b) {
+        sets[b].sc_base = (uint32_t)rsc;
+        sets[b].node_base = (uint32_t)rnd;
+        for (uint32_t k = 0; k < sets[b].nsc; ++k) sc_set[rsc + k] = (uint32_t)b;
+        rsc += sets[b].nsc;
+        rnd += sets[b].nsc > 0 ? tree_nodes(sets[b].nsc) + 1 : 0;
+    }
+    if (threadIdx.x == 0) bc->nsc = (uint32_t)tsc;
+}
+
+__global__ void __launch_bounds__(kFiltThreads) bx_filter_scatter_kernel(const float *__restrict__ pts, void *ws,
+                                                                         Layout L, BatchLayout BL)
+{
+    __shared__ uint32_t s_off[kFiltItems][NW];
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *tile_set = at<uint32_t>(ws, BL.tile_set);
+    const unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
+    unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
+    const uint32_t T = bc->tiles;
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const unsigned long long st = status[t];
+        if ((st & 0xffffffffull) == 0) continue;   // block-uniform
+        const int64_t b = tile_set[t];
+        const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
+        const uint32_t keep = bits[(size_t)t * kFiltThreads + threadIdx.x];
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin;
+        float px[kFiltItems], py[kFiltItems];
+#pragma unroll
+        for (int r = 0; r < kFiltItems; ++r) {
+            px[r] = py[r] = 0.0f;
+            if ((keep >> r) & 1u) {
+                const float2 v = p2[lo + r * kFiltThreads + threadIdx.x];
+                px[r] = v.x;
+                py[r] = v.y;
+            }
+        }
+        row_counts<1>(keep, s_off);
+        __syncthreads();
+        if (threadIdx.x < 32) scan_rows_warp0<1>(s_off);
+        __syncthreads();
+        scatter_tile<1, true>(keep, lo, st >> 32, s_off, px, py, nullptr, nullptr, out_keys, out_pay);
+        __syncthreads();
+    }
+}
+
 template <class K>
 int occupancy(K kernel, int threads)
 {
@@ -475,6 +687,20 @@ cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L
                    : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v);
     return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v)
                : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v);
+}
+
+cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
+{
+    static int per_sm_c = occupancy(bx_filter_count_kernel, kFiltThreads);
+    static int per_sm_s = occupancy(bx_filter_scatter_kernel, kFiltThreads);
+    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_c, BL.tiles_max));
+    const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_s, BL.tiles_max));
+    probe_before(CH_K_FILTER, st);
+    bx_filter_count_kernel<<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, ws, L, BL);
+    bx_filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, BL);
+    bx_filter_scatter_kernel<<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, ws, L, BL);
+    probe_after(CH_K_FILTER, st);
+    return cudaGetLastError();
 }
 
 }  // namespace ch

@@ -36,4 +36,15 @@ cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);
 // monotone chain over the sorted survivors; writes the hull
 cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st);
 
+// ---- many sets (ch_hull_batched); every stage works per set
+// validates offsets (points beyond n_cap: CH_ERR_CAPACITY) and maps tiles to sets
+cudaError_t launch_bx_setup(const int64_t *offsets, void *ws, const Layout &L, const BatchLayout &BL,
+                            int64_t n_cap, cudaStream_t st);
+cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
+cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
+cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
+cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
+cudaError_t launch_bx_finish(void *ws, const Layout &L, const BatchLayout &BL, uint32_t *hull_idx,
+                             int64_t *hull_offsets, cudaStream_t st);
+
 }  // namespace ch

@@ -20,6 +20,8 @@
 // digit-sorted, so stores are runs of consecutive addresses.  The payload
 // is staged in shared memory in element order and gathered through the
 // tile's inverse permutation at write-out, so it never occupies registers.
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -265,6 +267,183 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
     }
 }
 
+// ---------------------------------------------------------------------------
+// many sets (ch_hull_batched): every set's survivors form one contiguous
+// segment, sorted on its own.  Sort tiles are the sets' super-chunks (a
+// tile never spans two sets), digit histograms and digit starts are per
+// set, and a look-back chain starts afresh at each set's first tile.  All
+// four passes run (no skipping), so the result lands in buffer 0.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bx_sort_hist_kernel(void *ws, Layout L, BatchLayout BL)
+{
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *sc_set = at<uint32_t>(ws, BL.sc_set);
+    uint32_t *hist = at<uint32_t>(ws, BL.hist);
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    uint32_t *status0 = at<uint32_t>(ws, L.sort_status[0]);
+    const uint32_t nsc = bc->nsc;
+    {
+        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (int64_t w = gtid; w < (int64_t)nsc * 256; w += (int64_t)gridDim.x * blockDim.x) status0[w] = 0u;
+    }
+    __shared__ uint32_t sh[kSortPasses][256];
+    for (uint32_t j = blockIdx.x; j < nsc; j += gridDim.x) {
+        for (int i = threadIdx.x; i < kSortPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
+        __syncthreads();
+        const uint32_t b = sc_set[j];
+        const int64_t lo = (int64_t)(j - sets[b].sc_base) * kSortTile;
+        const int64_t n_t = min((int64_t)kSortTile, (int64_t)sets[b].s - lo);
+        const uint32_t *kt = keys + sets[b].surv_base + lo;
+        for (int64_t i = threadIdx.x; i < n_t; i += blockDim.x) {
+            const uint32_t k = kt[i];
+#pragma unroll
+            for (int p = 0; p < kSortPasses; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSortPasses * 256; i += blockDim.x) {
+            const uint32_t c = (&sh[0][0])[i];
+            if (c) atomicAdd(&hist[(size_t)b * kSortPasses * 256 + i], c);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads, 3) bx_sort_pass_kernel(void *ws, Layout L, BatchLayout BL, int p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+    BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    if (bc->abort) return;
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *sc_set = at<uint32_t>(ws, BL.sc_set);
+    const uint32_t *hist = at<uint32_t>(ws, BL.hist);
+    const int64_t ntiles = bc->nsc;
+    const uint32_t src = (uint32_t)p & 1u, dst = src ^ 1u;
+    const uint32_t *kin = at<uint32_t>(ws, L.keys[src]);
+    const unsigned long long *pin = at<unsigned long long>(ws, L.pay[src]);
+    uint32_t *kout = at<uint32_t>(ws, L.keys[dst]);
+    unsigned long long *pout = at<unsigned long long>(ws, L.pay[dst]);
+    uint32_t *status = at<uint32_t>(ws, L.sort_status[src]);
+    uint32_t *status_next = at<uint32_t>(ws, L.sort_status[dst]);
+    const int shift = 8 * p;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    {
+        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+        const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t w = gtid; w < ntiles * 256; w += gthreads) status_next[w] = 0u;
+    }
+    for (;;) {
+        if (tid == 0) sm.tile = atomicAdd(&bc->sort_ticket[p], 1u);
+        for (int d = lane; d < 256; d += 32) sm.wh[warp][d] = 0u;
+        __syncthreads();
+        const int64_t tile = sm.tile;
+        if (tile >= ntiles) break;
+        const uint32_t b = sc_set[tile];
+        const int64_t ltile = tile - sets[b].sc_base;
+        const uint64_t seg = sets[b].surv_base;
+        const uint32_t seg_n = sets[b].s;
+        const int64_t base = (int64_t)seg + ltile * kSortTile;
+        const uint32_t tile_n = (uint32_t)min((int64_t)kSortTile, (int64_t)seg_n - ltile * kSortTile);
+        {   // this set's digit starts
+            uint32_t ex;
+            block_excl_scan256(hist[((size_t)b * kSortPasses + p) * 256 + tid], ex, sm.warp_tot);
+            sm.dbase[tid] = ex;
+        }
+        uint32_t k[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+            if (e < tile_n) {
+                k[j] = __ldcs(kin + base + e);
+                sm.pay[e] = __ldcs(pin + base + e);
+            } else {
+                k[j] = 0u;
+            }
+        }
+        uint16_t rank[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+            const bool ok = e < tile_n;
+            const uint32_t d = ok ? (k[j] >> shift) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = __popc(peers & lt);
+            uint32_t cur = 0;
+            if (ok) cur = sm.wh[warp][d];
+            __syncwarp();
+            if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
+            __syncwarp();
+            rank[j] = (uint16_t)(cur + before);
+        }
+        __syncthreads();
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = sm.wh[w][tid];
+            sm.wh[w][tid] = cnt;
+            cnt += c;
+        }
+        uint32_t tstart;
+        block_excl_scan256(cnt, tstart, sm.warp_tot);
+        sm.tstart[tid] = tstart;
+        {
+            const uint32_t d = tid;
+            uint32_t *mine = status + tile * 256 + d;
+            uint32_t excl = 0;
+            if (ltile == 0) {   // the set's first tile
+                st_release_u32(mine, kFlagP32 | cnt);
+            } else {
+                st_release_u32(mine, kFlagA32 | cnt);
+                int64_t t = tile - 1;   // stays inside the set: its first tile publishes a prefix
+                uint32_t spins = 0;
+                bool failed = false;
+                while (t >= 0) {
+                    uint32_t st = ld_acquire_u32(status + t * 256 + d);
+                    while ((st >> 30) == 0u) {
+                        if (++spins > kSpinLimit || (spins > 1024 && error_set(ws, L))) {
+                            failed = true;
+                            break;
+                        }
+                        if (spins > 64) __nanosleep(100);
+                        st = ld_acquire_u32(status + t * 256 + d);
+                    }
+                    if (failed) break;
+                    excl += st & kVal32;
+                    if ((st >> 30) == 2u) break;
+                    --t;
+                }
+                if (failed) set_error(ws, L, kErrTimeout, 40 + p);
+                st_release_u32(mine, kFlagP32 | ((excl + cnt) & kVal32));
+            }
+            sm.gbase[d] = sm.dbase[d] + excl - tstart;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+            if (e < tile_n) {
+                const uint32_t d = (k[j] >> shift) & 255u;
+                const uint32_t pos = sm.tstart[d] + sm.wh[warp][d] + rank[j];
+                sm.keys[pos] = k[j];
+                sm.inv[pos] = (uint16_t)e;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+            const uint32_t key = sm.keys[i];
+            const uint32_t d = (key >> shift) & 255u;
+            const uint32_t pos = sm.gbase[d] + i;   // position inside the set
+            if (pos < seg_n) {
+                kout[seg + pos] = key;
+                pout[seg + pos] = sm.pay[sm.inv[i]];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int pass_blocks_per_sm()
 {
     static int cached = 0;
@@ -277,7 +456,40 @@ int pass_blocks_per_sm()
     return cached;
 }
 
+int bx_pass_blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(bx_sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SortSmem));
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, bx_sort_pass_kernel, kSortThreads, sizeof(SortSmem));
+        cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
 }  // namespace
+
+cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
+{
+    const int64_t cap = BL.tiles_max;
+    const int64_t hb = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sm_count() * 4));
+    probe_before(CH_K_SORT_HIST, st);
+    bx_sort_hist_kernel<<<(unsigned)hb, 256, 0, st>>>(ws, L, BL);
+    probe_after(CH_K_SORT_HIST, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t pb = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sm_count() * bx_pass_blocks_per_sm()));
+    for (int p = 0; p < kSortPasses; ++p) {
+        probe_before(CH_K_SORT_PASS, st);
+        bx_sort_pass_kernel<<<(unsigned)pb, kSortThreads, sizeof(SortSmem), st>>>(ws, L, BL, p);
+        probe_after(CH_K_SORT_PASS, st);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st)
 {

@@ -53,3 +53,26 @@ def test_host_argument_errors():
     assert lib.ch_hull(8, 1 << 30, 16, 32, 256, 1 << 40, None) == ch.CH_ERR_CAPACITY
     assert lib.ch_hull(8, 10, 16, None, 256, 1 << 20, None) == ch.CH_ERR_ARG
     assert lib.ch_last_error(None, None) == ch.CH_ERR_ARG
+
+
+def test_workspace_size_grows_with_sets():
+    one = ch.ch_workspace_size(10**6, 1)
+    many = ch.ch_workspace_size(10**6, 4096)
+    assert many > one
+    # per-set state is bounded: a few hundred bytes plus one ragged tile's
+    # chain buffers per set
+    assert many - one < 4096 * 200 * 1024
+
+
+def test_batched_host_argument_errors():
+    lib = ch.load()
+    big = 1 << 40
+    # hull_batched(pts, offsets, num_sets, hull_idx, hull_offsets, ws, ws_bytes, stream)
+    assert lib.ch_hull_batched(8, 8, -1, 16, 8, 256, big, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_batched(8, None, 4, 16, 8, 256, big, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_batched(8, 8, 4, 16, None, 256, big, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_batched(8, 12, 4, 16, 8, 256, big, None) == ch.CH_ERR_ARG    # offsets misaligned
+    assert lib.ch_hull_batched(None, 8, 4, 16, 8, 256, big, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_batched(8, 8, 4, 16, 8, None, big, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_batched(8, 8, 4, 16, 8, 100, big, None) == ch.CH_ERR_ARG     # ws misaligned
+    assert lib.ch_hull_batched(8, 8, 4, 16, 8, 256, 1024, None) == ch.CH_ERR_CAPACITY
