@@ -144,8 +144,9 @@ def algorithmic_bytes(kernel, n, s_list):
 
 
 def load_traffic(kernel):
-    """ncu DRAM bytes per launch recorded under profiles/, if the kernel
-    source is unchanged since the capture."""
+    """ncu DRAM bytes of a captured launch of `kernel`, as a ratio to that
+    launch's algorithmic bytes, recorded under profiles/ -- None when the
+    kernel's source file changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -307,7 +308,8 @@ def run_ours(args):
             tr = load_traffic(dominant)
             roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                    "traffic": int(tr["dram_per_algorithmic_byte"] * per_launch_bytes) if tr else None,
+                    "traffic_source": tr["capture"] if tr else None,
                     "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4)}
 
     # filter-only throughput (the paper's headline stage) from its own launches

@@ -99,8 +99,16 @@ ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hul
  * ch_hull, to hull_idx[hull_offsets[b] ..], with hull_offsets (device,
  * num_sets+1 entries) the exclusive prefix sum of the hull sizes.
  * hull_idx capacity: offsets[num_sets] entries.  ws must be sized with
- * ch_workspace_size(offsets[num_sets], num_sets).  Not part of the paper:
- * the batched form of the same path. */
+ * ch_workspace_size(N, num_sets) for some N >= offsets[num_sets]; since the
+ * offsets live on the device, the host derives the point capacity from
+ * ws_bytes and the device checks the offsets against it.  num_sets == 0
+ * writes hull_offsets[0] = 0.  Device-side errors (reported by
+ * ch_last_error; hull_offsets are then all 0): malformed offsets
+ * (offsets[0] != 0, a negative or decreasing entry) CH_ERR_ARG, more points
+ * than the workspace holds CH_ERR_CAPACITY.  A set with a non-finite
+ * coordinate gets an empty hull and CH_ERR_NONFINITE is reported; the
+ * other sets are still computed.  Total points < 2^30.  Not part of the
+ * paper: the batched form of the same path (Algorithm 1 per set). */
 ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_sets,
                           uint32_t *hull_idx, int64_t *hull_offsets,
                           void *ws, size_t ws_bytes, void *stream);
@@ -150,16 +158,22 @@ typedef enum {
     CH_K_COUNT = 8
 } ch_kernel_id;
 
-/* Start timing: every later launch of a kernel whose bit (1 << id) is set in
- * kernel_mask is bracketed by two CUDA events recorded on its launch stream,
- * for at most max_launches launches per kernel.  Launch counting for all
- * kernels restarts at zero.  Host-only bookkeeping; creates the events. */
+/* Start timing: every later launch group of a kernel id whose bit (1 << id)
+ * is set in kernel_mask is bracketed by two CUDA events recorded on its
+ * launch stream, for at most max_launches groups per id.  A group is the
+ * kernels one step launches back to back under that id: one for
+ * EXTREMES, OCTAGON, SORT_HIST, SORT_PASS (one per pass), EMIT, FINISH;
+ * three for FILTER with the two-pass schedule (count, scan, scatter), one
+ * with the single pass; two for CHAIN (chains, tree merge).  Kernel-launch
+ * counting for all ids restarts at zero.  Host-only bookkeeping; creates
+ * the events. */
 ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
 
 /* Stop timing: waits for the recorded events, writes per kernel id the summed
  * event-measured milliseconds (ms[CH_K_COUNT], 0 when not timed) and the
- * number of launches since ch_probe_start (launches[CH_K_COUNT]), and
- * releases the events.  Either pointer may be NULL. */
+ * number of kernels launched under it since ch_probe_start, in every
+ * stream (launches[CH_K_COUNT]), and releases the events.  Either pointer
+ * may be NULL. */
 ch_status ch_probe_stop(double *ms, int64_t *launches);
 
 #ifdef __cplusplus

@@ -185,6 +185,7 @@ cudaError_t launch_bx_setup(const int64_t *offsets, void *ws, const Layout &L, c
     bx_setup_kernel<<<1, kSetupThreads, 0, st>>>(offsets, ws, L, BL, n_cap);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(BL.tiles_max, 256), sm_count() * 4));
     bx_tileset_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws, BL);
+    note_kernels(CH_K_EXTREMES, 2);
     return cudaGetLastError();
 }
 
@@ -195,6 +196,7 @@ cudaError_t launch_bx_finish(void *ws, const Layout &L, const BatchLayout &BL, u
     bx_hullsize_kernel<<<1, kSetupThreads, 0, st>>>(ws, BL, hull_offsets);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.n, 256), sm_count() * 4));
     bx_assemble_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws, L, BL, hull_offsets, hull_idx);
+    note_kernels(CH_K_FINISH, 2);
     probe_after(CH_K_FINISH, st);
     return cudaGetLastError();
 }

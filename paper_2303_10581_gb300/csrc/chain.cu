@@ -853,6 +853,7 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
     probe_before(CH_K_CHAIN, st);
     chain_kernel<<<(unsigned)cb, LT, sizeof(ChainSmem), st>>>(ws, L);
     chain_merge_kernel<<<(unsigned)ceil_div(L.n_chunks, 32), 32, 0, st>>>(ws, L);
+    note_kernels(CH_K_CHAIN, 2);
     probe_after(CH_K_CHAIN, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -861,6 +862,7 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
     if (eb < 1) eb = 1;
     probe_before(CH_K_EMIT, st);
     emit_kernel<<<(unsigned)eb, kEmitThreads, 0, st>>>(ws, L, hull_idx);
+    note_kernels(CH_K_EMIT, 1);
     probe_after(CH_K_EMIT, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -869,6 +871,7 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
     if (fb < 1) fb = 1;
     probe_before(CH_K_FINISH, st);
     finish_kernel<<<(unsigned)fb, 256, 0, st>>>(ws, L, hull_idx, hull_count);
+    note_kernels(CH_K_FINISH, 1);
     probe_after(CH_K_FINISH, st);
     return cudaGetLastError();
 }
@@ -889,6 +892,7 @@ cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cu
     probe_before(CH_K_CHAIN, st);
     bx_chain_kernel<<<(unsigned)cb, LT, sizeof(ChainSmem), st>>>(ws, L, BL);
     bx_merge_kernel<<<(unsigned)ceil_div(BL.tiles_max, 32), 32, 0, st>>>(ws, L, BL);
+    note_kernels(CH_K_CHAIN, 2);
     probe_after(CH_K_CHAIN, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -897,6 +901,7 @@ cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cu
     if (eb < 1) eb = 1;
     probe_before(CH_K_EMIT, st);
     bx_emit_kernel<<<(unsigned)eb, kEmitThreads, 0, st>>>(ws, L, BL);
+    note_kernels(CH_K_EMIT, 1);
     probe_after(CH_K_EMIT, st);
     return cudaGetLastError();
 }

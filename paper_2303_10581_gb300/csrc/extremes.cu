@@ -414,6 +414,7 @@ cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, cons
     probe_before(CH_K_EXTREMES, st);
     bx_extremes_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(pts, ws, L, BL);
     bx_octagon_kernel<<<(unsigned)ceil_div(BL.num_sets, 8), 256, 0, st>>>(pts, ws, L, BL);
+    note_kernels(CH_K_EXTREMES, 2);
     probe_after(CH_K_EXTREMES, st);
     return cudaGetLastError();
 }
@@ -444,6 +445,7 @@ cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout 
     probe_before(CH_K_EXTREMES, st);
     extremes_kernel<<<(unsigned)blocks, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, build_polygon ? 1 : 0,
                                                               zero_ptr, zero_words);
+    note_kernels(CH_K_EXTREMES, 1);
     probe_after(CH_K_EXTREMES, st);
     return cudaGetLastError();
 }
@@ -457,6 +459,7 @@ cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, vo
     if (blocks < 1) blocks = 1;
     probe_before(CH_K_OCTAGON, st);
     octagon_kernel<<<(unsigned)blocks, 256, 0, st>>>(pts, n, ext8, ws, L, zero_ptr, zero_words);
+    note_kernels(CH_K_OCTAGON, 1);
     probe_after(CH_K_OCTAGON, st);
     return cudaGetLastError();
 }

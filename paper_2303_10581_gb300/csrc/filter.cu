@@ -642,6 +642,7 @@ cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, ntiles);
     filter_kernel<G, KEYS><<<(unsigned)std::max<int64_t>(blocks, 1), kFiltThreads, 0, st>>>(
         pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
+    note_kernels(CH_K_FILTER, 1);
     return cudaGetLastError();
 }
 
@@ -658,6 +659,7 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, n, KEYS ? 1 : 0, surv_count);
     filter_scatter_kernel<G, KEYS><<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx,
                                                                           reinterpret_cast<float2 *>(surv_pts));
+    note_kernels(CH_K_FILTER, 3);
     return cudaGetLastError();
 }
 
@@ -699,6 +701,7 @@ cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const 
     bx_filter_count_kernel<<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, ws, L, BL);
     bx_filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, BL);
     bx_filter_scatter_kernel<<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, ws, L, BL);
+    note_kernels(CH_K_FILTER, 3);
     probe_after(CH_K_FILTER, st);
     return cudaGetLastError();
 }

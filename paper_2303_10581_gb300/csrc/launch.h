@@ -13,6 +13,8 @@ int sm_count();
 
 // instrumentation around every launch (probe.cu)
 void probe_before(int kid, cudaStream_t st);
+// counts `count` kernel launches of kernel id kid (every launcher calls it)
+void note_kernels(int kid, int count);
 void probe_after(int kid, cudaStream_t st);
 
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,

@@ -128,6 +128,160 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
     }
 }
 
+// Exclusive prefix of digit d over the tiles before `tile` (within its
+// segment): adds the published counts going back to the first inclusive
+// prefix, kLookWin status words per round trip.  A status word carries its
+// flag and count together and nothing else is published through it, so
+// relaxed accesses suffice.
+constexpr int kLookWin = 8;
+
+__device__ __forceinline__ uint32_t digit_lookback(const uint32_t *status, int64_t tile, uint32_t d, void *ws,
+                                                   const Layout &L, uint32_t site)
+{
+    uint32_t excl = 0, spins = 0;
+    int64_t t = tile - 1;
+    for (;;) {
+        uint32_t v[kLookWin];
+#pragma unroll
+        for (int i = 0; i < kLookWin; ++i) v[i] = t - i >= 0 ? ld_relaxed_u32(status + (t - i) * 256 + d) : kFlagP32;
+        bool stop = false, done = false;
+        int used = 0;
+#pragma unroll
+        for (int i = 0; i < kLookWin; ++i) {
+            if (!stop) {
+                const uint32_t f = v[i] >> 30;
+                if (f == 0u) {
+                    stop = true;
+                } else {
+                    excl += v[i] & kVal32;
+                    ++used;
+                    if (f == 2u) stop = done = true;
+                }
+            }
+        }
+        if (done) return excl;
+        t -= used;
+        if (used < kLookWin) {   // the next tile has published nothing yet
+            if (++spins > kSpinLimit || (spins > 1024 && error_set(ws, L))) {
+                set_error(ws, L, kErrTimeout, site);
+                return excl;
+            }
+            if (spins > 64) __nanosleep(100);
+        }
+    }
+}
+
+struct PassIO {
+    const uint32_t *kin;
+    const unsigned long long *pin;
+    uint32_t *kout;
+    unsigned long long *pout;
+    uint32_t *status;   // 256 digit status words per tile
+};
+
+// One tile of a pass: tile_n <= 4096 (key, payload) pairs from element
+// `base`, ranked stably by digit (key >> shift) & 255 and written to
+// out_base + (segment digit start + rank in digit).  `first`: the
+// segment's first tile (its prefix is its own count).  Expects sm.dbase
+// (the segment's digit starts) set and sm.wh cleared, behind a barrier.
+__device__ __forceinline__ void pass_tile(SortSmem &sm, const PassIO &io, int64_t tile, int64_t base,
+                                          uint32_t tile_n, int64_t out_base, uint32_t out_n, int shift, bool first,
+                                          void *ws, const Layout &L, uint32_t site)
+{
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    // keys to registers, payload to shared memory (element order)
+    uint32_t k[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+        if (e < tile_n) {
+            k[j] = __ldcs(io.kin + base + e);
+            sm.pay[e] = __ldcs(io.pin + base + e);
+        } else {
+            k[j] = 0u;
+        }
+    }
+    // stable rank inside the warp, items in element order (j, lane)
+    uint16_t rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+        const bool ok = e < tile_n;
+        const uint32_t d = ok ? (k[j] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = __popc(peers & lt);
+        uint32_t cur = 0;
+        if (ok) cur = sm.wh[warp][d];
+        __syncwarp();
+        if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[j] = (uint16_t)(cur + before);
+    }
+    __syncthreads();
+    // per digit: exclusive offsets across warps and the tile count
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t c = sm.wh[w][tid];
+        sm.wh[w][tid] = cnt;
+        cnt += c;
+    }
+    uint32_t tstart;
+    block_excl_scan256(cnt, tstart, sm.warp_tot);
+    sm.tstart[tid] = tstart;
+    // decoupled look-back per digit (thread tid owns digit tid)
+    {
+        const uint32_t d = tid;
+        uint32_t *mine = io.status + tile * 256 + d;
+        uint32_t excl = 0;
+        if (first) {
+            st_relaxed_u32(mine, kFlagP32 | cnt);
+        } else {
+            st_relaxed_u32(mine, kFlagA32 | cnt);
+            excl = digit_lookback(io.status, tile, d, ws, L, site);
+            st_relaxed_u32(mine, kFlagP32 | ((excl + cnt) & kVal32));
+        }
+        sm.gbase[d] = sm.dbase[d] + excl - tstart;
+    }
+    // digit-sorted keys and the inverse permutation
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
+        if (e < tile_n) {
+            const uint32_t d = (k[j] >> shift) & 255u;
+            const uint32_t pos = sm.tstart[d] + sm.wh[warp][d] + rank[j];
+            sm.keys[pos] = k[j];
+            sm.inv[pos] = (uint16_t)e;
+        }
+    }
+    __syncthreads();
+    // runs of equal digit go to consecutive addresses; the bound check only
+    // matters after a look-back wait gave up
+    if (tile_n == kSortTile) {
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const uint32_t i = j * kSortThreads + tid;
+            const uint32_t key = sm.keys[i];
+            const uint32_t pos = sm.gbase[(key >> shift) & 255u] + i;
+            if (pos < out_n) {
+                io.kout[out_base + pos] = key;
+                io.pout[out_base + pos] = sm.pay[sm.inv[i]];
+            }
+        }
+    } else {
+        for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+            const uint32_t key = sm.keys[i];
+            const uint32_t pos = sm.gbase[(key >> shift) & 255u] + i;
+            if (pos < out_n) {
+                io.kout[out_base + pos] = key;
+                io.pout[out_base + pos] = sm.pay[sm.inv[i]];
+            }
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, Layout L, int p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,15 +292,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
     if (s == 0 || ctrl->pass_skip[p]) return;
     const uint32_t src = ctrl->pass_src[p], dst = src ^ 1u;
     const int64_t ntiles = ceil_div((int64_t)s, kSortTile);
-    const uint32_t *kin = at<uint32_t>(ws, L.keys[src]);
-    const unsigned long long *pin = at<unsigned long long>(ws, L.pay[src]);
-    uint32_t *kout = at<uint32_t>(ws, L.keys[dst]);
-    unsigned long long *pout = at<unsigned long long>(ws, L.pay[dst]);
-    uint32_t *status = at<uint32_t>(ws, L.sort_status[src]);
+    const PassIO io{at<uint32_t>(ws, L.keys[src]), at<unsigned long long>(ws, L.pay[src]),
+                    at<uint32_t>(ws, L.keys[dst]), at<unsigned long long>(ws, L.pay[dst]),
+                    at<uint32_t>(ws, L.sort_status[src])};
     uint32_t *status_next = at<uint32_t>(ws, L.sort_status[dst]);
-    const int shift = 8 * p;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    const uint32_t lt = (1u << lane) - 1u;
 
     // clear the digit status of the next executed pass
     {
@@ -160,7 +310,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
         block_excl_scan256(ctrl->hist[p][tid], ex, sm.warp_tot);
         sm.dbase[tid] = ex;
     }
-
     for (;;) {
         if (tid == 0) sm.tile = atomicAdd(&ctrl->sort_ticket[p], 1u);
         for (int d = lane; d < 256; d += 32) sm.wh[warp][d] = 0u;
@@ -168,102 +317,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
         const int64_t tile = sm.tile;
         if (tile >= ntiles) break;
         const int64_t base = tile * kSortTile;
-        const uint32_t tile_n = (uint32_t)min((int64_t)kSortTile, (int64_t)s - base);
-
-        // keys to registers, payload to shared memory (element order)
-        uint32_t k[kSortItems];
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            if (e < tile_n) {
-                k[j] = __ldcs(kin + base + e);
-                sm.pay[e] = __ldcs(pin + base + e);
-            } else {
-                k[j] = 0u;
-            }
-        }
-        // stable rank inside the warp, items in element order (j, lane)
-        uint16_t rank[kSortItems];
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            const bool ok = e < tile_n;
-            const uint32_t d = ok ? (k[j] >> shift) & 255u : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = __popc(peers & lt);
-            uint32_t cur = 0;
-            if (ok) cur = sm.wh[warp][d];
-            __syncwarp();
-            if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
-            __syncwarp();
-            rank[j] = (uint16_t)(cur + before);
-        }
-        __syncthreads();
-        // per digit: exclusive offsets across warps and the tile count
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t c = sm.wh[w][tid];
-            sm.wh[w][tid] = cnt;
-            cnt += c;
-        }
-        uint32_t tstart;
-        block_excl_scan256(cnt, tstart, sm.warp_tot);
-        sm.tstart[tid] = tstart;
-        // decoupled look-back per digit (thread tid owns digit tid)
-        {
-            const uint32_t d = tid;
-            uint32_t *mine = status + tile * 256 + d;
-            uint32_t excl = 0;
-            if (tile == 0) {
-                st_release_u32(mine, kFlagP32 | cnt);
-            } else {
-                st_release_u32(mine, kFlagA32 | cnt);
-                int64_t t = tile - 1;
-                uint32_t spins = 0;
-                bool failed = false;
-                while (t >= 0) {
-                    uint32_t st = ld_acquire_u32(status + t * 256 + d);
-                    while ((st >> 30) == 0u) {
-                        if (++spins > kSpinLimit || (spins > 1024 && error_set(ws, L))) {
-                            failed = true;
-                            break;
-                        }
-                        if (spins > 64) __nanosleep(100);
-                        st = ld_acquire_u32(status + t * 256 + d);
-                    }
-                    if (failed) break;
-                    excl += st & kVal32;
-                    if ((st >> 30) == 2u) break;
-                    --t;
-                }
-                if (failed) set_error(ws, L, kErrTimeout, 20 + p);
-                st_release_u32(mine, kFlagP32 | ((excl + cnt) & kVal32));
-            }
-            sm.gbase[d] = sm.dbase[d] + excl - tstart;
-        }
-        // digit-sorted keys and the inverse permutation
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            if (e < tile_n) {
-                const uint32_t d = (k[j] >> shift) & 255u;
-                const uint32_t pos = sm.tstart[d] + sm.wh[warp][d] + rank[j];
-                sm.keys[pos] = k[j];
-                sm.inv[pos] = (uint16_t)e;
-            }
-        }
-        __syncthreads();
-        for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-            const uint32_t key = sm.keys[i];
-            const uint32_t d = (key >> shift) & 255u;
-            const uint32_t pos = sm.gbase[d] + i;
-            if (pos < s) {   // always true unless a look-back wait gave up
-                kout[pos] = key;
-                pout[pos] = sm.pay[sm.inv[i]];
-            }
-        }
-        __syncthreads();
+        pass_tile(sm, io, tile, base, (uint32_t)min((int64_t)kSortTile, (int64_t)s - base), 0, s, 8 * p, tile == 0,
+                  ws, L, 20 + p);
     }
 }
 
@@ -321,15 +376,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) bx_sort_pass_kernel(void *ws,
     const uint32_t *hist = at<uint32_t>(ws, BL.hist);
     const int64_t ntiles = bc->nsc;
     const uint32_t src = (uint32_t)p & 1u, dst = src ^ 1u;
-    const uint32_t *kin = at<uint32_t>(ws, L.keys[src]);
-    const unsigned long long *pin = at<unsigned long long>(ws, L.pay[src]);
-    uint32_t *kout = at<uint32_t>(ws, L.keys[dst]);
-    unsigned long long *pout = at<unsigned long long>(ws, L.pay[dst]);
-    uint32_t *status = at<uint32_t>(ws, L.sort_status[src]);
+    const PassIO io{at<uint32_t>(ws, L.keys[src]), at<unsigned long long>(ws, L.pay[src]),
+                    at<uint32_t>(ws, L.keys[dst]), at<unsigned long long>(ws, L.pay[dst]),
+                    at<uint32_t>(ws, L.sort_status[src])};
     uint32_t *status_next = at<uint32_t>(ws, L.sort_status[dst]);
-    const int shift = 8 * p;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    const uint32_t lt = (1u << lane) - 1u;
     {
         const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
         const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -343,104 +394,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) bx_sort_pass_kernel(void *ws,
         if (tile >= ntiles) break;
         const uint32_t b = sc_set[tile];
         const int64_t ltile = tile - sets[b].sc_base;
-        const uint64_t seg = sets[b].surv_base;
+        const int64_t seg = (int64_t)sets[b].surv_base;
         const uint32_t seg_n = sets[b].s;
-        const int64_t base = (int64_t)seg + ltile * kSortTile;
-        const uint32_t tile_n = (uint32_t)min((int64_t)kSortTile, (int64_t)seg_n - ltile * kSortTile);
-        {   // this set's digit starts
+        {   // this set's digit starts (the scan's barriers also order sm.wh)
             uint32_t ex;
             block_excl_scan256(hist[((size_t)b * kSortPasses + p) * 256 + tid], ex, sm.warp_tot);
             sm.dbase[tid] = ex;
         }
-        uint32_t k[kSortItems];
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            if (e < tile_n) {
-                k[j] = __ldcs(kin + base + e);
-                sm.pay[e] = __ldcs(pin + base + e);
-            } else {
-                k[j] = 0u;
-            }
-        }
-        uint16_t rank[kSortItems];
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            const bool ok = e < tile_n;
-            const uint32_t d = ok ? (k[j] >> shift) & 255u : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t before = __popc(peers & lt);
-            uint32_t cur = 0;
-            if (ok) cur = sm.wh[warp][d];
-            __syncwarp();
-            if (ok && before == 0) sm.wh[warp][d] = cur + __popc(peers);
-            __syncwarp();
-            rank[j] = (uint16_t)(cur + before);
-        }
-        __syncthreads();
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t c = sm.wh[w][tid];
-            sm.wh[w][tid] = cnt;
-            cnt += c;
-        }
-        uint32_t tstart;
-        block_excl_scan256(cnt, tstart, sm.warp_tot);
-        sm.tstart[tid] = tstart;
-        {
-            const uint32_t d = tid;
-            uint32_t *mine = status + tile * 256 + d;
-            uint32_t excl = 0;
-            if (ltile == 0) {   // the set's first tile
-                st_release_u32(mine, kFlagP32 | cnt);
-            } else {
-                st_release_u32(mine, kFlagA32 | cnt);
-                int64_t t = tile - 1;   // stays inside the set: its first tile publishes a prefix
-                uint32_t spins = 0;
-                bool failed = false;
-                while (t >= 0) {
-                    uint32_t st = ld_acquire_u32(status + t * 256 + d);
-                    while ((st >> 30) == 0u) {
-                        if (++spins > kSpinLimit || (spins > 1024 && error_set(ws, L))) {
-                            failed = true;
-                            break;
-                        }
-                        if (spins > 64) __nanosleep(100);
-                        st = ld_acquire_u32(status + t * 256 + d);
-                    }
-                    if (failed) break;
-                    excl += st & kVal32;
-                    if ((st >> 30) == 2u) break;
-                    --t;
-                }
-                if (failed) set_error(ws, L, kErrTimeout, 40 + p);
-                st_release_u32(mine, kFlagP32 | ((excl + cnt) & kVal32));
-            }
-            sm.gbase[d] = sm.dbase[d] + excl - tstart;
-        }
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const uint32_t e = warp * (32 * kSortItems) + j * 32 + lane;
-            if (e < tile_n) {
-                const uint32_t d = (k[j] >> shift) & 255u;
-                const uint32_t pos = sm.tstart[d] + sm.wh[warp][d] + rank[j];
-                sm.keys[pos] = k[j];
-                sm.inv[pos] = (uint16_t)e;
-            }
-        }
-        __syncthreads();
-        for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-            const uint32_t key = sm.keys[i];
-            const uint32_t d = (key >> shift) & 255u;
-            const uint32_t pos = sm.gbase[d] + i;   // position inside the set
-            if (pos < seg_n) {
-                kout[seg + pos] = key;
-                pout[seg + pos] = sm.pay[sm.inv[i]];
-            }
-        }
-        __syncthreads();
+        pass_tile(sm, io, tile, seg + ltile * kSortTile,
+                  (uint32_t)min((int64_t)kSortTile, (int64_t)seg_n - ltile * kSortTile), seg, seg_n, 8 * p,
+                  ltile == 0, ws, L, 40 + p);
     }
 }
 
@@ -477,6 +440,7 @@ cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cud
     const int64_t hb = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sm_count() * 4));
     probe_before(CH_K_SORT_HIST, st);
     bx_sort_hist_kernel<<<(unsigned)hb, 256, 0, st>>>(ws, L, BL);
+    note_kernels(CH_K_SORT_HIST, 1);
     probe_after(CH_K_SORT_HIST, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -484,6 +448,7 @@ cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cud
     for (int p = 0; p < kSortPasses; ++p) {
         probe_before(CH_K_SORT_PASS, st);
         bx_sort_pass_kernel<<<(unsigned)pb, kSortThreads, sizeof(SortSmem), st>>>(ws, L, BL, p);
+        note_kernels(CH_K_SORT_PASS, 1);
         probe_after(CH_K_SORT_PASS, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -499,6 +464,7 @@ cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st)
     if (hb < 1) hb = 1;
     probe_before(CH_K_SORT_HIST, st);
     sort_hist_kernel<<<(unsigned)hb, 256, 0, st>>>(ws, L);
+    note_kernels(CH_K_SORT_HIST, 1);
     probe_after(CH_K_SORT_HIST, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -508,6 +474,7 @@ cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st)
     for (int p = 0; p < kSortPasses; ++p) {
         probe_before(CH_K_SORT_PASS, st);
         sort_pass_kernel<<<(unsigned)pb, kSortThreads, sizeof(SortSmem), st>>>(ws, L, p);
+        note_kernels(CH_K_SORT_PASS, 1);
         probe_after(CH_K_SORT_PASS, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
