@@ -64,6 +64,25 @@ def dist_env():
     return rank, world, local
 
 
+# --------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x, device):
+    """The maximum of x over all ranks of the default process group (x
+    itself when there is none)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, points_per_rank_step, ms_max):
+    """Whole-job Gpoints/s: every rank processes its own replica of the
+    workload, the job takes as long as its slowest rank."""
+    return world * points_per_rank_step / (ms_max * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- inputs
 
 def make_inputs(n, seed):
@@ -285,12 +304,9 @@ def run_ours(args):
     clk = clocks.stop()
     ws.check()
     ms = t0.elapsed_time(t1) / args.steps
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dev)
     pts_per_step = len(DISTS) * n
-    value = world * pts_per_step / (ms_max * 1e-3) / 1e9
+    value = job_rate(world, pts_per_step, ms_max)
     launches_per_step = sum(v[1] for v in probe.values()) / args.steps
 
     # roofline of the dominant kernel
@@ -348,12 +364,8 @@ def run_ours(args):
         for _ in range(args.steps):
             d2h = e2e_step()
         barrier()
-        e_ms = (time.perf_counter() - w0) * 1e3 / args.steps
-        t = torch.tensor([e_ms], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-        e2e = {"value": round(world * pts_per_step / (e_ms * 1e-3) / 1e9, 3), "unit": "Gpoints/s",
+        e_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / args.steps, dev)
+        e2e = {"value": round(job_rate(world, pts_per_step, e_ms), 3), "unit": "Gpoints/s",
                "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": 8 * n * len(DISTS),
                "d2h_bytes_per_step": d2h}
 
