@@ -311,7 +311,19 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
         sm.dbase[tid] = ex;
     }
     for (;;) {
-        if (tid == 0) sm.tile = atomicAdd(&ctrl->sort_ticket[p], 1u);
+        if (tid == 0) {
+            const uint32_t t = atomicAdd(&ctrl->sort_ticket[p], 1u);
+            sm.tile = t;
+            // tickets go out in order, one per block and tile: the tile one
+            // grid ahead is taken about one tile-time from now (by whichever
+            // block); stream it into L2 meanwhile
+            const int64_t ahead = (int64_t)t + gridDim.x;
+            if (ahead < ntiles) {
+                const uint32_t nn = (uint32_t)min((int64_t)kSortTile, (int64_t)s - ahead * kSortTile);
+                bulk_prefetch_l2(io.kin + ahead * kSortTile, (nn * 4u) & ~15u);
+                bulk_prefetch_l2(io.pin + ahead * kSortTile, (nn * 8u) & ~15u);
+            }
+        }
         for (int d = lane; d < 256; d += 32) sm.wh[warp][d] = 0u;
         __syncthreads();
         const int64_t tile = sm.tile;
