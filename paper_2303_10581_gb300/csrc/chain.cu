@@ -144,6 +144,7 @@ struct ChainSmem {
     float prev_x;
     int has_prev;
     int seq_len;
+    int wcur, wdone;              // single-warp passes: buffer and convergence
 };
 
 // leaf c's entries start at flat[lb[c]]; its stack holds offsets from there
@@ -539,7 +540,7 @@ __device__ void superchunk(ChainSmem &sm, const ChainPtrs &P, int64_t j, int64_t
             const int len = sm.seq_len;
             // ---- per warp: its share of the sequence, [warp * S, warp * S + S)
             const int S = (len + NWB - 1) / NWB;
-            const int w0 = warp * S;
+            int w0 = warp * S;
             int wl = max(0, min(S, len - w0));   // this warp's live length
             uint16_t *flat = &sm.list[0][0];
             int cur = 0;                          // 0: list[0], 2: list[2]
@@ -563,6 +564,95 @@ __device__ void superchunk(ChainSmem &sm, const ChainPtrs &P, int64_t j, int64_t
                 const bool done = kept == wl;
                 wl = kept;
                 if (done) break;
+            }
+            // ---- block level: the warps' survivors concatenated in list[2],
+            // then passes over the whole sequence.  A sequence whose every
+            // turn is strict is its own chain: no leaves, no merges.
+            if (cur == 2)
+                for (int i = lane; i < wl; i += 32) flat[w0 + i] = flat[2 * NL + w0 + i];
+            if (lane == 0) sm.wsum[warp] = (uint32_t)wl;
+            __syncthreads();
+            {
+                int off = 0, tot = 0;
+#pragma unroll
+                for (int w = 0; w < NWB; ++w) {
+                    const int u = (int)sm.wsum[w];
+                    if (w < warp) off += u;
+                    tot += u;
+                }
+                for (int i = lane; i < wl; i += 32) flat[2 * NL + off + i] = flat[w0 + i];
+                __syncthreads();
+                int blen = tot, bcur = 2;
+                bool chain_done = blen <= 2;
+                // long: all threads, block-wide compaction
+                for (int bp = 0; bp < kBlockElimPasses && !chain_done && blen > kWarpSeqMax; ++bp) {
+                    const uint16_t *src = flat + bcur * NL;
+                    const int bl = blen;
+                    const int kept = block_compact(
+                        sm, bl,
+                        [&](int j) {
+                            return j == 0 || j == bl - 1 ||
+                                   !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
+                        },
+                        [&](int j) { return src[j]; }, flat + (2 - bcur) * NL);
+                    bcur = 2 - bcur;
+                    chain_done = kept == bl || kept <= 2;
+                    blen = kept;
+                }
+                if (!chain_done && blen <= kWarpSeqMax) {
+                    // short: one warp runs the passes, no block barriers
+                    if (warp == 0) {
+                        int bl = blen, wc = bcur, done = 0;
+                        for (int bp = 0; bp < kBlockElimPasses && !done; ++bp) {
+                            const uint16_t *src = flat + wc * NL;
+                            uint16_t *dst = flat + (2 - wc) * NL;
+                            int kept = 0;
+                            for (int c0 = 0; c0 < bl; c0 += 32) {
+                                const int j = c0 + lane;
+                                bool k = false;
+                                if (j < bl)
+                                    k = j == 0 || j == bl - 1 ||
+                                        !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
+                                const uint32_t m = __ballot_sync(0xffffffffu, k);
+                                if (k) dst[kept + __popc(m & lt)] = src[j];
+                                kept += __popc(m);
+                            }
+                            __syncwarp();
+                            wc = 2 - wc;
+                            done = kept == bl || kept <= 2;
+                            bl = kept;
+                        }
+                        if (lane == 0) {
+                            sm.seq_len = bl;
+                            sm.wcur = wc;
+                            sm.wdone = done;
+                        }
+                    }
+                    __syncthreads();
+                    blen = sm.seq_len;
+                    bcur = sm.wcur;
+                    chain_done = sm.wdone != 0;
+                }
+                if (chain_done) {   // write the chain and go to the other side
+                    uint32_t *dpos = P.pos[side] + sc * CS;
+                    float2 *dpt = P.pt[side] + sc * CS;
+                    for (int q = t; q < blen; q += LT) {
+                        const int e = flat[bcur * NL + q];
+                        dpos[q] = e < SC ? (uint32_t)(base + e) : sm.ext_pos[e - SC];
+                        dpt[q] = sm.pts[e];
+                    }
+                    if (t == 0) {
+                        P.lo[side][sc] = 0;
+                        P.hi[side][sc] = blen - 1;
+                    }
+                    __syncthreads();
+                    continue;
+                }
+                // not yet a chain: leaves and merges over the block's sequence
+                const int S2 = (blen + NWB - 1) / NWB;
+                w0 = warp * S2;
+                wl = max(0, min(S2, blen - w0));
+                cur = bcur;
             }
             // ---- leaf chains: lane l takes [l * LW, l * LW + LW) of the warp's list
             const int LW = (wl + 31) / 32;

@@ -28,7 +28,9 @@ constexpr int kLeafC = 16;            // points per leaf chain (one thread)
 constexpr int kChainThreads = 256;    // leaves per super-chunk (one block)
 constexpr int kChainC = kLeafC * kChainThreads;   // 4096 points per super-chunk
 constexpr int kChainStride = kChainC + 8;          // chain slots per super-chunk (up to kChainC + 1 used)
-constexpr int kElimPasses = 12;       // cap on the parallel elimination passes
+constexpr int kElimPasses = 12;       // cap on the per-warp elimination passes
+constexpr int kBlockElimPasses = 24;  // cap on the passes over a super-chunk's whole sequence
+constexpr int kWarpSeqMax = 256;      // whole-sequence passes run in one warp up to this length
 constexpr int kEmitThreads = 256;     // chunks per emit tile (one per thread)
 constexpr int64_t kMaxHullN = (int64_t)1 << 30;
 constexpr int64_t kMaxN = ((int64_t)1 << 32) - 1;
