@@ -68,6 +68,47 @@ __device__ __forceinline__ bool drop(int side, const float2 &a, const float2 &b,
     return side == 0 ? o <= 0 : o >= 0;
 }
 
+// One strict-turn elimination pass of a warp over the sequence
+// src[0 .. len) of point indices (its two ends always stay): the kept
+// entries go to dst in order; returns how many.  len >= 3.  Two 32-entry
+// chunks per step, binary32 tier of both tests first, so their latencies
+// overlap.
+__device__ __forceinline__ int warp_elim_pass(const float2 *pts, const uint16_t *src, uint16_t *dst, int len,
+                                              int side, int lane, uint32_t lt)
+{
+    int kept = 0;
+    for (int c0 = 0; c0 < len; c0 += 64) {
+        int j[2];
+        bool test[2];
+        float2 a[2], b[2], c[2];
+        int o[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            j[u] = c0 + 32 * u + lane;
+            test[u] = j[u] > 0 && j[u] < len - 1;
+            const int jj = test[u] ? j[u] : 1;
+            a[u] = pts[src[jj - 1]];
+            b[u] = pts[src[jj]];
+            c[u] = pts[src[jj + 1]];
+            o[u] = orient_f32(a[u].x, a[u].y, b[u].x, b[u].y, c[u].x, c[u].y);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (test[u] && o[u] == 2) o[u] = orient_rest(a[u].x, a[u].y, b[u].x, b[u].y, c[u].x, c[u].y);
+        uint32_t m[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const bool drop_it = test[u] && (side == 0 ? o[u] <= 0 : o[u] >= 0);
+            const bool k = j[u] < len && !drop_it;
+            m[u] = __ballot_sync(0xffffffffu, k);
+            if (k) dst[kept + __popc(m[u] & lt)] = src[j[u]];
+            kept += __popc(m[u]);
+        }
+    }
+    __syncwarp();
+    return kept;
+}
+
 // ---------------------------------------------------------------------------
 // tangent walk, shared by the in-block and the global merge
 // ---------------------------------------------------------------------------
@@ -546,20 +587,8 @@ __device__ void superchunk(ChainSmem &sm, const ChainPtrs &P, int64_t j, int64_t
             int cur = 0;                          // 0: list[0], 2: list[2]
             // elimination passes over the warp's segment; its two ends stay
             for (int pass = 0; pass < kElimPasses && wl > 2; ++pass) {
-                const uint16_t *src = flat + cur * NL + w0;
-                uint16_t *dst = flat + (2 - cur) * NL + w0;
-                int kept = 0;
-                for (int c0 = 0; c0 < wl; c0 += 32) {
-                    const int j = c0 + lane;
-                    bool k = false;
-                    if (j < wl)
-                        k = j == 0 || j == wl - 1 ||
-                            !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
-                    const uint32_t m = __ballot_sync(0xffffffffu, k);
-                    if (k) dst[kept + __popc(m & lt)] = src[j];
-                    kept += __popc(m);
-                }
-                __syncwarp();
+                const int kept = warp_elim_pass(sm.pts, flat + cur * NL + w0, flat + (2 - cur) * NL + w0, wl, side,
+                                                lane, lt);
                 cur = 2 - cur;
                 const bool done = kept == wl;
                 wl = kept;
@@ -604,20 +633,8 @@ __device__ void superchunk(ChainSmem &sm, const ChainPtrs &P, int64_t j, int64_t
                     if (warp == 0) {
                         int bl = blen, wc = bcur, done = 0;
                         for (int bp = 0; bp < kBlockElimPasses && !done; ++bp) {
-                            const uint16_t *src = flat + wc * NL;
-                            uint16_t *dst = flat + (2 - wc) * NL;
-                            int kept = 0;
-                            for (int c0 = 0; c0 < bl; c0 += 32) {
-                                const int j = c0 + lane;
-                                bool k = false;
-                                if (j < bl)
-                                    k = j == 0 || j == bl - 1 ||
-                                        !drop(side, sm.pts[src[j - 1]], sm.pts[src[j]], sm.pts[src[j + 1]]);
-                                const uint32_t m = __ballot_sync(0xffffffffu, k);
-                                if (k) dst[kept + __popc(m & lt)] = src[j];
-                                kept += __popc(m);
-                            }
-                            __syncwarp();
+                            const int kept =
+                                warp_elim_pass(sm.pts, flat + wc * NL, flat + (2 - wc) * NL, bl, side, lane, lt);
                             wc = 2 - wc;
                             done = kept == bl || kept <= 2;
                             bl = kept;

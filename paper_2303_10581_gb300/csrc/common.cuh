@@ -403,20 +403,31 @@ __device__ __forceinline__ int orient_near(float ax, float ay, float bx, float b
 // for the rounding of the bound itself, and 2^-140 absorbs the absolute
 // error of products that fall into the subnormal range.  Undecided cases
 // try tier 1b, then tier 2.
-__device__ __forceinline__ int orient(float ax, float ay, float bx, float by, float cx, float cy)
+// The binary32 tier alone, branch-free: the sign when the bound proves it,
+// 2 otherwise.
+__device__ __forceinline__ int orient_f32(float ax, float ay, float bx, float by, float cx, float cy)
 {
     float detleft = __fmul_rn(__fsub_rn(ax, cx), __fsub_rn(by, cy));
     float detright = __fmul_rn(__fsub_rn(ay, cy), __fsub_rn(bx, cx));
     float det = __fsub_rn(detleft, detright);
     float detsum = __fadd_rn(fabsf(detleft), fabsf(detright));
     float eb = __fmaf_ru(detsum, 2.384185791015625e-07f /* 2^-22 */, 7.174648137343064e-43f /* 2^-140 */);
-    if (detsum <= 3.0e38f) {
-        if (det > eb) return 1;
-        if (-det > eb) return -1;
-    }
+    const int o = det > eb ? 1 : (-det > eb ? -1 : 2);
+    return detsum <= 3.0e38f ? o : 2;
+}
+
+// The tiers after binary32: exact differences, binary64, expansions.
+__device__ __forceinline__ int orient_rest(float ax, float ay, float bx, float by, float cx, float cy)
+{
     const int o = orient_near(ax, ay, bx, by, cx, cy);
     if (o != 2) return o;
     return orient_d(ax, ay, bx, by, cx, cy);
+}
+
+__device__ __forceinline__ int orient(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    const int o = orient_f32(ax, ay, bx, by, cx, cy);
+    return o != 2 ? o : orient_rest(ax, ay, bx, by, cx, cy);
 }
 
 // ---------------------------------------------------------------------------
