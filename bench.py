@@ -54,6 +54,9 @@ def parse():
                     help="subset of the workload's distributions (profiling runs)")
     ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
                     help="compaction schedule: 0 two passes, 1 single pass with look-back")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="single: the three 1e8 sets; batched: 4096 uneven sets, batched call vs per-set calls")
+    ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     return ap.parse_args()
 
 
@@ -395,9 +398,105 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH_WORKLOAD = ("{B} independent sets, sizes log-uniform in [1e2, 1e6] points, distribution drawn from "
+                  "normal / circle / displaced circle, scaled by U[0.1, 10], rotated by U[0, 2 pi)")
+
+
+def run_batched(args):
+    """The batched workload: one ch_hull_batched call (direct, and replayed
+    from a CUDA graph) against one ch_hull call per set, end to end on
+    resident inputs; the per-set hulls of both must agree exactly."""
+    import numpy as np
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    import pointgen
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B = args.sets
+    pts, offsets, _ = pointgen.make_batch(B, seed=args.seed)
+    n = len(pts)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_off = torch.from_numpy(offsets).to(dev)
+    stream = torch.cuda.current_stream()
+    ws = ch.Workspace(n, num_sets=B, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    hoff = torch.zeros(B + 1, dtype=torch.int64, device=dev)
+    sizes = np.diff(offsets)
+    ws1 = ch.Workspace(int(sizes.max()), device=dev)
+    idx1 = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt1 = torch.zeros(B, dtype=torch.int32, device=dev)
+    views = [(d_pts[offsets[b]:offsets[b + 1]], idx1[offsets[b]:offsets[b + 1]], cnt1[b:b + 1]) for b in range(B)]
+
+    def batched():
+        ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf, stream)
+
+    def per_set():
+        for v, o, c in views:
+            if v.shape[0]:
+                ch.ch_hull(v, o, c, ws1.buf, stream)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    for _ in range(args.warmup):
+        batched()
+        per_set()
+    ws.check()
+    ws1.check()
+    # both forms give the same hull for every set
+    h_b = hoff.cpu().numpy()
+    ib = idx.cpu().numpy()
+    i1 = idx1.cpu().numpy()
+    c1 = cnt1.cpu().numpy()
+    for b in range(B):
+        assert h_b[b + 1] - h_b[b] == c1[b], b
+        assert np.array_equal(ib[h_b[b]:h_b[b + 1]], i1[offsets[b]:offsets[b] + c1[b]]), b
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf)
+    graph.replay()
+    torch.cuda.synchronize()
+    ws.check()
+    assert np.array_equal(hoff.cpu().numpy(), h_b)
+
+    ms_batched = timed(batched, args.steps)
+    ms_graph = timed(graph.replay, args.steps)
+    ms_loop = timed(per_set, max(1, args.steps // 2))
+    ch.ch_probe_start(ch.KERNELS, max_launches=64)
+    batched()
+    launches = sum(v[1] for v in ch.ch_probe_stop().values())
+    ws.check()
+    line = {
+        "metric": "end-to-end hull time of a batch of uneven sets: batched call vs one call per set",
+        "value": round(ms_graph, 4), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f32+exact", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(B=B), "points": int(n), "sets": B,
+                   "largest_set": int(sizes.max()), "hull_vertices": int(h_b[-1])},
+        "batched_graph_ms": round(ms_graph, 4), "batched_ms": round(ms_batched, 4),
+        "per_set_calls_ms": round(ms_loop, 4), "speedup_vs_per_set": round(ms_loop / ms_graph, 2),
+        "gpoints_s": round(n / (ms_graph * 1e-3) / 1e9, 3), "gpu_launches_per_batch": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global DISTS
     args = parse()
+    if args.workload == "batched":
+        run_batched(args)
+        return
     DISTS = tuple(d for d in args.dists.split(",") if d)
     assert DISTS and all(d in ALL_DISTS for d in DISTS), args.dists
     if args.impl == "reference":

@@ -156,3 +156,32 @@ def test_nonfinite_set_gets_an_empty_hull_and_the_others_are_exact():
     for b in (0, 1, 3, 4):
         want = oracle.convex_hull(sets[b])[2]
         assert np.array_equal(idx[hoff[b]:hoff[b + 1]], want)
+
+
+def test_cuda_graph_replay():
+    """The batched call captures into a CUDA graph (no allocation, no host
+    synchronisation); replays read the current contents of the buffers."""
+    pts, offsets, _ = pointgen.make_batch(64, seed=31, min_n=50, max_n=20_000)
+    d = torch.from_numpy(pts).cuda()
+    o = torch.from_numpy(offsets).cuda()
+    ws = ch.Workspace(len(pts), num_sets=64)
+    idx = torch.empty(len(pts), dtype=torch.int32, device="cuda")
+    hoff = torch.zeros(65, dtype=torch.int64, device="cuda")
+    ch.ch_hull_batched(d, o, idx, hoff, ws.buf)   # first call outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ch.ch_hull_batched(d, o, idx, hoff, ws.buf)
+    for seed in (31, 32):
+        p2, off2, _ = pointgen.make_batch(64, seed=31, min_n=50, max_n=20_000)
+        if seed == 32:   # same set sizes, new coordinates
+            p2 = (p2 * np.float32(-1.5)).astype(np.float32)
+        d.copy_(torch.from_numpy(p2))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert ch.ch_last_error(ws.buf) == ch.CH_OK
+        h = hoff.cpu().numpy()
+        got = idx.cpu().numpy().view(np.uint32)
+        for b in range(64):
+            want = oracle.convex_hull(p2[offsets[b]:offsets[b + 1]])[2]
+            assert np.array_equal(got[h[b]:h[b + 1]], want), (seed, b)
