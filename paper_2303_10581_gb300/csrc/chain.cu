@@ -750,8 +750,16 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     const int64_t nsc = ceil_div((int64_t)s, SC);
-    for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x)
+    for (int64_t sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
+        // the block's next super-chunk streams into L2 meanwhile
+        const int64_t nxt = sc + gridDim.x;
+        if (threadIdx.x == 0 && nxt < nsc) {
+            const uint32_t nn = (uint32_t)min((int64_t)SC, (int64_t)s - nxt * SC);
+            bulk_prefetch_l2(P.keys + nxt * SC, (nn * 4u) & ~15u);
+            bulk_prefetch_l2(P.pay + nxt * SC, (nn * 8u) & ~15u);
+        }
         superchunk(sm, P, sc, sc * SC, (int)min((int64_t)SC, (int64_t)s - sc * SC), 0, s);
+    }
 }
 
 // Global merge tree over the super-chunks: one thread per super-chunk
