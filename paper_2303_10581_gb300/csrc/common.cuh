@@ -20,6 +20,7 @@ constexpr int kExtThreads = 512;      // extremes sweep
 constexpr int kFiltThreads = 256;     // fused test + compaction
 constexpr int kFiltItems = 16;        // points per thread per tile
 constexpr int kFiltTile = kFiltThreads * kFiltItems;   // 4096 points = 32 KB
+constexpr int kFiltMaxBlocks = 4096;                  // grid cap of the two-pass filter
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys
@@ -115,6 +116,7 @@ struct Layout {
     size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
     size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
     size_t keep_bits;       // u16[filt_tiles * kFiltThreads]: keep decisions of the count pass
+    size_t filt_bsum;       // u32[kFiltMaxBlocks]: survivors per block of the count pass
     size_t utmp;          // u32[n]
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
@@ -224,6 +226,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.chunk = take((size_t)L.n_chunks * 8 * 4);
     L.node = take((size_t)L.n_nodes * 4 * 4);
     L.keep_bits = take((size_t)L.filt_tiles * kFiltThreads * 2);
+    L.filt_bsum = take((size_t)kFiltMaxBlocks * 4);
     L.utmp = take((size_t)n * 4);
     L.total = o;
     return L;

@@ -65,6 +65,78 @@ __device__ __forceinline__ bool keep_point(const Octagon &o, float x, float y)
 
 constexpr int NW = kFiltThreads / 32;
 
+// A point's first look: 0 discard (inside the quick-discard rectangle), 1
+// keep (proven not strictly left of the edge facing it), 2 deferred (likely
+// strictly inside: every edge must be tested).
+__device__ __forceinline__ uint32_t first_look(const Octagon &o, float x, float y)
+{
+    if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) return 0u;
+    if (!o.has_edges) return 1u;
+    const float ux = x - o.cx, uy = y - o.cy;
+    int e;
+    if (uy >= 0.0f) {
+        if (ux >= 0.0f) e = ux >= uy ? 0 : 1;
+        else e = uy >= -ux ? 2 : 3;
+    } else {
+        if (ux < 0.0f) e = -ux >= -uy ? 4 : 5;
+        else e = -uy >= ux ? 6 : 7;
+    }
+    if (!((o.valid >> e) & 1u)) return 2u;
+    const float u = __fsub_rn(x, o.ax[e]);
+    const float v = __fsub_rn(y, o.ay[e]);
+    const float t = __fsub_rn(__fmul_rn(o.dx[e], v), __fmul_rn(o.dy[e], u));
+    return t < -o.bound[e] ? 1u : 2u;
+}
+
+// Deferred points, spread over the lanes, would hold whole warps in the
+// edge loop; each warp queues them (lane, item) and tests them 32 at a
+// time after its items' first look, re-reading each point (an L2 hit).
+constexpr uint32_t kDeferCap = 32 * kFiltItems;   // every item of the warp
+
+struct FiltQueue {
+    uint32_t cnt;
+    uint16_t tag[kDeferCap];   // lane << 4 | item
+    uint32_t res[32];          // kept item bits, per lane
+};
+
+__device__ __forceinline__ void queue_reset(FiltQueue &q)
+{
+    const uint32_t lane = lane_id();
+    q.res[lane] = 0u;
+    if (lane == 0) q.cnt = 0u;
+    __syncwarp();
+}
+
+// Records item `item` of this lane as deferred (the queue holds every item
+// of the warp, so it cannot overflow).
+__device__ __forceinline__ void defer(FiltQueue &q, uint32_t item)
+{
+    const uint32_t slot = atomicAdd(&q.cnt, 1u);
+    q.tag[slot] = (uint16_t)((lane_id() << 4) | item);
+}
+
+// Tests the queued points (all lanes); returns this lane's keep bits among
+// them and leaves the queue empty.  load(lane, item) reads a point of this
+// warp.
+template <class LoadPoint>
+__device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon &so, bool deferred, LoadPoint load)
+{
+    if (!__any_sync(0xffffffffu, deferred)) return 0u;   // the common case: nothing queued
+    __syncwarp();
+    const uint32_t total = q.cnt, lane = lane_id();
+    if (total == 0u) return 0u;
+    for (uint32_t i = lane; i < total; i += 32) {
+        const uint32_t tg = q.tag[i];
+        const float2 v = load(tg >> 4, tg & 15u);
+        if (keep_point(so, v.x, v.y)) atomicOr(&q.res[tg >> 4], 1u << (tg & 15u));
+    }
+    __syncwarp();
+    const uint32_t r = q.res[lane];
+    __syncwarp();
+    queue_reset(q);
+    return r;
+}
+
 // Copies the polygon to shared memory; false when the call was aborted
 // (non-finite input or a bad vertex index).
 __device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout &L)
@@ -82,7 +154,8 @@ __device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout
 // (bit r * G + h); positions past n are not kept.
 template <int G>
 __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int64_t n, int64_t base,
-                                              const Octagon &so, float (&px)[kFiltItems], float (&py)[kFiltItems])
+                                              const Octagon &so, float (&px)[kFiltItems], float (&py)[kFiltItems],
+                                              FiltQueue &fq)
 {
     constexpr int ROWS = kFiltItems / G;
     const uint32_t tid = threadIdx.x;
@@ -111,9 +184,19 @@ __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int
                 py[r] = v[r].y;
             }
         }
+        bool deferred = false;
 #pragma unroll
-        for (int q = 0; q < kFiltItems; ++q)
-            if (keep_point(so, px[q], py[q])) keep |= 1u << q;
+        for (int q = 0; q < kFiltItems; ++q) {
+            const uint32_t c = first_look(so, px[q], py[q]);
+            if (c == 2u) deferred = true;
+            if (c == 1u) keep |= 1u << q;
+            else if (c == 2u) defer(fq, (uint32_t)q);
+        }
+        const uint32_t wbase = tid & ~31u;
+        keep |= resolve_deferred(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+            const int64_t i = base + (int64_t)((item / G) * kFiltThreads + wbase + ln) * G + item % G;
+            return reinterpret_cast<const float2 *>(pts)[i];
+        });
     } else {
         const float2 *p2 = reinterpret_cast<const float2 *>(pts);
 #pragma unroll
@@ -229,6 +312,8 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
                                                               uint32_t *__restrict__ surv_count)
 {
     __shared__ Octagon so;
+    __shared__ FiltQueue s_fq[NW];
+    queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_off[kFiltItems / G][NW];
     __shared__ uint32_t s_tile;
     __shared__ unsigned long long s_excl;
@@ -249,7 +334,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
         if (tile >= ntiles) break;
         const int64_t base = tile * kFiltTile;
         float px[kFiltItems], py[kFiltItems];
-        const uint32_t keep = load_test<G>(pts, n, base, so, px, py);
+        const uint32_t keep = load_test<G>(pts, n, base, so, px, py, s_fq[threadIdx.x >> 5]);
         row_counts<G>(keep, s_off);
         __syncthreads();
         if (warp == 0) {
@@ -287,15 +372,22 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
                                                                     void *ws, Layout L)
 {
     __shared__ Octagon so;
+    __shared__ FiltQueue s_fq[NW];
+    queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_w[NW];
     if (!load_octagon(so, ws, L)) return;
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     const int64_t ntiles = ceil_div(n, kFiltTile);
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // a contiguous range of tiles per block, so the scatter pass finds
+    // every tile's output offset from the block totals and its own range
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
+    uint32_t block_total = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
         float px[kFiltItems], py[kFiltItems];
-        const uint32_t keep = load_test<G>(pts, n, tile * kFiltTile, so, px, py);
+        const uint32_t keep = load_test<G>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
         bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
         uint32_t c = __popc(keep);
 #pragma unroll
@@ -307,72 +399,109 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
 #pragma unroll
             for (int w = 0; w < NW; ++w) t += s_w[w];
             status[tile] = t;
+            block_total += t;
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = block_total;
 }
 
-// One block: exclusive scan of the tile counts, in place; the total is the
-// survivor count.
-__global__ void __launch_bounds__(1024) filter_scan_kernel(void *ws, Layout L, int64_t n, int keys,
-                                                           uint32_t *surv_count)
-{
-    __shared__ uint64_t s_w[32];
-    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    if (at<Octagon>(ws, L.oct)->abort) {
-        if (threadIdx.x == 0) write_count(keys, ctrl, surv_count, 0);
-        return;
-    }
-    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
-    const int64_t ntiles = ceil_div(n, kFiltTile);
-    const int64_t per = ceil_div(ntiles, (int64_t)blockDim.x);
-    const int64_t t0 = threadIdx.x * per, t1 = min(t0 + per, ntiles);
-    uint64_t sum = 0;
-    for (int64_t t = t0; t < t1; ++t) sum += status[t] & 0xffffffffull;
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    uint64_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += u;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint64_t before = 0, total = 0;
-    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-        if (w < warp) before += s_w[w];
-        total += s_w[w];
-    }
-    uint64_t run = before + incl - sum;
-    for (int64_t t = t0; t < t1; ++t) {
-        const uint64_t c = status[t] & 0xffffffffull;
-        status[t] = (run << 32) | c;
-        run += c;
-    }
-    if (threadIdx.x == 0) write_count(keys, ctrl, surv_count, (uint32_t)total);
-}
-
+// Second pass, launched with the count pass's grid: block b owns the same
+// tile range.  Its output offset is the sum of the earlier blocks' totals;
+// an in-block scan of its tiles' counts gives each tile's offset, and only
+// tiles with survivors are visited.  Block 0 writes the survivor count.
 template <int G, bool KEYS>
 __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const float *__restrict__ pts, int64_t n,
                                                                       void *ws, Layout L,
                                                                       uint32_t *__restrict__ surv_idx,
-                                                                      float2 *__restrict__ surv_pts)
+                                                                      float2 *__restrict__ surv_pts,
+                                                                      uint32_t *surv_count)
 {
     __shared__ uint32_t s_off[kFiltItems / G][NW];
     __shared__ uint32_t s_abort;
+    __shared__ uint32_t s_red[2][NW];
+    __shared__ uint32_t s_list[kFiltThreads];    // non-empty tiles of a chunk: offset in chunk
+    __shared__ uint32_t s_loff[kFiltThreads];    // and their output offsets
+    __shared__ uint32_t s_nlist;
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     if (threadIdx.x == 0) s_abort = at<Octagon>(ws, L.oct)->abort;
     __syncthreads();
-    if (s_abort) return;
+    if (s_abort) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) write_count(KEYS, ctrl, surv_count, 0);
+        return;
+    }
     const unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
     const uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
     unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    const uint32_t tid = threadIdx.x;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const unsigned long long st = status[tile];
-        if ((st & 0xffffffffull) == 0) continue;   // block-uniform
-        const int64_t base = tile * kFiltTile;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    // offset of this block's range, and the total
+    uint32_t before = 0, total = 0;
+    for (uint32_t i = tid; i < gridDim.x; i += kFiltThreads) {
+        const uint32_t v = bsum[i];
+        total += v;
+        if (i < blockIdx.x) before += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = before;
+        s_red[1][warp] = total;
+    }
+    __syncthreads();
+    before = total = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        before += s_red[0][w];
+        total += s_red[1][w];
+    }
+    if (blockIdx.x == 0 && tid == 0) write_count(KEYS, ctrl, surv_count, total);
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(ntiles, r0 + per);
+    uint32_t run = before;
+    for (int64_t c0 = r0; c0 < r1; c0 += kFiltThreads) {
+        // this chunk's tile counts: exclusive scan and the non-empty ones
+        const int64_t t = c0 + tid;
+        const uint32_t cnt = t < r1 ? (uint32_t)(status[t] & 0xffffffffull) : 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
+        }
+        const uint32_t nz = __ballot_sync(0xffffffffu, cnt != 0u);
+        if (lane == 31) {
+            s_red[0][warp] = incl;
+            s_red[1][warp] = __popc(nz);
+        }
+        __syncthreads();
+        uint32_t wbefore = 0, chunk_total = 0, lbefore = 0, nlist = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (w < (int)warp) {
+                wbefore += s_red[0][w];
+                lbefore += s_red[1][w];
+            }
+            chunk_total += s_red[0][w];
+            nlist += s_red[1][w];
+        }
+        if (cnt != 0u) {
+            const uint32_t slot = lbefore + __popc(nz & ((1u << lane) - 1u));
+            s_list[slot] = tid;
+            s_loff[slot] = run + wbefore + incl - cnt;
+        }
+        if (tid == 0) s_nlist = nlist;
+        __syncthreads();
+        const uint32_t nl = s_nlist;
+        for (uint32_t li = 0; li < nl; ++li) {
+            const int64_t tile = c0 + s_list[li];
+            const uint32_t out_off = s_loff[li];
+            const int64_t base = tile * kFiltTile;
         const uint32_t keep = bits[tile * kFiltThreads + tid];
         // coordinates of the kept points only (the decisions are stored)
         float px[kFiltItems], py[kFiltItems];
@@ -404,12 +533,14 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
                 }
             }
         }
-        row_counts<G>(keep, s_off);
-        __syncthreads();
-        if (threadIdx.x < 32) scan_rows_warp0<G>(s_off);
-        __syncthreads();
-        scatter_tile<G, KEYS>(keep, base, st >> 32, s_off, px, py, surv_idx, surv_pts, out_keys, out_pay);
-        __syncthreads();
+            row_counts<G>(keep, s_off);
+            __syncthreads();
+            if (threadIdx.x < 32) scan_rows_warp0<G>(s_off);
+            __syncthreads();
+            scatter_tile<G, KEYS>(keep, base, out_off, s_off, px, py, surv_idx, surv_pts, out_keys, out_pay);
+            __syncthreads();
+        }
+        run += chunk_total;
     }
 }
 
@@ -420,9 +551,10 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
 // Thread t tests points lo + r * 256 + t of the set (r < 16), below hi.
 __device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, int64_t lo, int64_t hi,
                                                  const Octagon &so, float (&px)[kFiltItems],
-                                                 float (&py)[kFiltItems])
+                                                 float (&py)[kFiltItems], FiltQueue &fq)
 {
     uint32_t keep = 0;
+    bool deferred = false;
 #pragma unroll
     for (int r = 0; r < kFiltItems; ++r) {
         const int64_t i = lo + r * kFiltThreads + threadIdx.x;
@@ -431,10 +563,16 @@ __device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, 
             const float2 v = __ldcs(p2 + i);
             px[r] = v.x;
             py[r] = v.y;
-            if (keep_point(so, v.x, v.y)) keep |= 1u << r;
+            const uint32_t c = first_look(so, v.x, v.y);
+            if (c == 2u) deferred = true;
+            if (c == 1u) keep |= 1u << r;
+            else if (c == 2u) defer(fq, (uint32_t)r);
         }
     }
-    return keep;
+    const uint32_t wbase = threadIdx.x & ~31u;
+    return keep | resolve_deferred(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+               return p2[lo + (int64_t)item * kFiltThreads + wbase + ln];
+           });
 }
 
 // Copies set b's polygon to shared memory when the block moves to a new set.
@@ -453,6 +591,8 @@ __global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const flo
                                                                        Layout L, BatchLayout BL)
 {
     __shared__ Octagon so;
+    __shared__ FiltQueue s_fq[NW];
+    queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_w[NW];
     const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
     if (bc->abort) return;
@@ -472,7 +612,8 @@ __global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const flo
             const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
             const int64_t hi = min(lo + kFiltTile, sets[b].n);
             float px[kFiltItems], py[kFiltItems];
-            keep = bx_load_test(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, lo, hi, so, px, py);
+            keep = bx_load_test(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, lo, hi, so, px, py,
+                                s_fq[threadIdx.x >> 5]);
         }
         bits[(size_t)t * kFiltThreads + threadIdx.x] = (uint16_t)keep;
         uint32_t c = __popc(keep);
@@ -651,15 +792,14 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
                             float *surv_pts, uint32_t *surv_count, cudaStream_t st)
 {
     static int per_sm_c = occupancy(filter_count_kernel<G>, kFiltThreads);
-    static int per_sm_s = occupancy(filter_scatter_kernel<G, KEYS>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_c, ntiles));
-    const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_s, ntiles));
+    // both passes use the same grid: block b owns the same tile range
+    const int64_t bc = std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
     filter_count_kernel<G><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
-    filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, n, KEYS ? 1 : 0, surv_count);
-    filter_scatter_kernel<G, KEYS><<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx,
-                                                                          reinterpret_cast<float2 *>(surv_pts));
-    note_kernels(CH_K_FILTER, 3);
+    filter_scatter_kernel<G, KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(
+        pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
+    note_kernels(CH_K_FILTER, 2);
     return cudaGetLastError();
 }
 
