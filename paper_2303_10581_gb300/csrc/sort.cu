@@ -244,6 +244,7 @@ __device__ __forceinline__ void pass_tile(SortSmem &sm, const PassIO &io, int64_
         }
         sm.gbase[d] = sm.dbase[d] + excl - tstart;
     }
+    __syncthreads();   // every digit's tstart is read below (gbase after the next barrier)
     // digit-sorted keys and the inverse permutation
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
