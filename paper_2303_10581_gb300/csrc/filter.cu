@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
         total += s_red[1][w];
     }
     if (blockIdx.x == 0 && tid == 0) write_count(KEYS, ctrl, surv_count, total);
+    __syncthreads();   // s_red is reused below
     const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
     const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(ntiles, r0 + per);
     uint32_t run = before;
