@@ -193,7 +193,8 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     if (sets > 0) {
         // every set adds at most one ragged tile / super-chunk, and each
         // set's merge tree has fewer than twice as many nodes as leaves
-        L.filt_tiles = L.sort_tiles = L.n_chunks = ceil_div(n, kChainC) + sets;
+        L.filt_tiles = L.n_chunks = ceil_div(n, kChainC) + sets;
+        L.sort_tiles = L.sort_tiles > L.n_chunks ? L.sort_tiles : L.n_chunks;
         L.n_nodes = 2 * L.n_chunks + sets;
     }
     L.emit_tiles = ceil_div(L.n_chunks, kEmitThreads);
