@@ -37,7 +37,7 @@ WORKLOAD = "hull of 3 single sets, n=1e8 fp32 each: normal(0,1), unit circle, di
 N_POINTS = 100_000_000
 ALL_DISTS = ("normal", "circle", "displaced")
 DISTS = ALL_DISTS
-KERNEL_IDS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish")
+KERNEL_IDS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
 def parse():

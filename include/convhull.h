@@ -145,7 +145,7 @@ ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32_t *ext8,
 ch_status ch_filter_variant(int32_t variant);
 
 /* ---- instrumentation (not part of the paper's method) ------------------
- * Kernel identifiers of the path, in launch order. */
+ * Kernel identifiers of the path. */
 typedef enum {
     CH_K_EXTREMES = 0,   /* Sec. 3.1 sweep (+ polygon build in its last block) */
     CH_K_OCTAGON = 1,    /* polygon build for ch_filter                        */
@@ -155,7 +155,9 @@ typedef enum {
     CH_K_CHAIN = 5,      /* Sec. 3.3 chunk chains + tree merges                 */
     CH_K_EMIT = 6,       /* compaction of the chain ranges                      */
     CH_K_FINISH = 7,     /* hull assembly                                       */
-    CH_K_COUNT = 8
+    CH_K_KGON = 8,       /* hull step: second polygon over the survivors
+                            (runs after FILTER, before SORT_HIST)             */
+    CH_K_COUNT = 9
 } ch_kernel_id;
 
 /* Start timing: every later launch group of a kernel id whose bit (1 << id)
@@ -163,8 +165,9 @@ typedef enum {
  * launch stream, for at most max_launches groups per id.  A group is the
  * kernels one step launches back to back under that id: one for
  * EXTREMES, OCTAGON, SORT_HIST, SORT_PASS (one per pass), EMIT, FINISH;
- * three for FILTER with the two-pass schedule (count, scan, scatter), one
- * with the single pass; two for CHAIN (chains, tree merge).  Kernel-launch
+ * two for FILTER with the two-pass schedule (count, scatter), one with the
+ * single pass; two for CHAIN (chains, tree merge); five for KGON (sample
+ * extremes, polygon, estimate, count, scatter).  Kernel-launch
  * counting for all ids restarts at zero.  Host-only bookkeeping; creates
  * the events. */
 ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);

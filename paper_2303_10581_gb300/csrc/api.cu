@@ -86,6 +86,7 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
                                     at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st);
     if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st);
+    if (e == cudaSuccess) e = launch_kgon(ws, L, st);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
     if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
     return cuda_status(e);

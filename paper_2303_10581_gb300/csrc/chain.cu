@@ -52,7 +52,6 @@ namespace ch {
 
 namespace {
 
-constexpr int LC = kLeafC;          // points per leaf
 constexpr int LT = kChainThreads;   // leaves per super-chunk
 constexpr int SC = kChainC;         // points per super-chunk
 constexpr int CS = kChainStride;    // chain slots per super-chunk

@@ -77,6 +77,21 @@ struct ExtCtrl {
     uint32_t nonfinite;               // a non-finite coordinate was seen
 };
 
+// second throw-away polygon of the hull step (kgon.cu)
+constexpr int kKgonDirs = 128;
+
+struct KgonCtrl {                         // zeroed with the control block
+    unsigned long long slot[kKgonDirs];   // packed (ord(dot) << 32 | ~position) per direction
+    uint32_t sample, inside;              // the estimate's sample and how much of it is inside
+    uint32_t s_in;                        // survivors entering the pass (0: the pass did not run)
+    uint32_t pad;
+};
+
+struct Kgon {                             // strictly convex, counter-clockwise; m < 3: unusable
+    uint32_t m, pad;
+    float vx[kKgonDirs], vy[kKgonDirs];
+};
+
 // control block: zeroed at the start of every call (together with the
 // filter's look-back status, which follows it)
 struct Ctrl {
@@ -90,7 +105,8 @@ struct Ctrl {
     uint32_t hist_done;
     uint32_t emit_ticket[2];
     uint32_t h_lower, h_upper;
-    uint32_t pad[2];
+    uint32_t sort_in;                 // buffer holding the survivors for the sort (0, or 1 after the polygon pass)
+    uint32_t pad;
 };
 
 // persistent words: survive calls, cleared by ch_last_error
@@ -104,6 +120,7 @@ struct Persist {
 struct Layout {
     size_t persist, extctrl, oct, ext8;
     size_t ctrl;            // Ctrl, immediately followed by
+    size_t kgon_ctrl;       // KgonCtrl,
     size_t filt_status;     // u64[filt_tiles],
     size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node, and
     size_t emit_status[2];  // u64[emit_tiles]: look-back of the chain compaction
@@ -117,6 +134,7 @@ struct Layout {
     size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
     size_t keep_bits;       // u16[filt_tiles * kFiltThreads]: keep decisions of the count pass
     size_t filt_bsum;       // u32[kFiltMaxBlocks]: survivors per block of the count pass
+    size_t kgon;            // Kgon
     size_t utmp;          // u32[n]
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
@@ -209,6 +227,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.oct = take(sizeof(Octagon));
     L.ext8 = take(8 * sizeof(uint32_t));
     L.ctrl = take(sizeof(Ctrl));
+    L.kgon_ctrl = take(sizeof(KgonCtrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
     L.node_cnt = take((size_t)L.n_nodes * 4);
     L.emit_status[0] = take((size_t)L.emit_tiles * 8);
@@ -228,6 +247,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.node = take((size_t)L.n_nodes * 4 * 4);
     L.keep_bits = take((size_t)L.filt_tiles * kFiltThreads * 2);
     L.filt_bsum = take((size_t)kFiltMaxBlocks * 4);
+    L.kgon = take(sizeof(Kgon));
     L.utmp = take((size_t)n * 4);
     L.total = o;
     return L;

@@ -32,6 +32,9 @@ cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
                           int variant = -1);
 
+// second throw-away polygon over the survivors (hull step; may do nothing)
+cudaError_t launch_kgon(void *ws, const Layout &L, cudaStream_t st);
+
 // stable LSD radix sort of the survivor (key, index) pairs held in ws
 cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);
 

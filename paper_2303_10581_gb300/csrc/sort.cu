@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
     const Octagon *oct = at<Octagon>(ws, L.oct);
     const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
     const int64_t ntiles = ceil_div((int64_t)s, kSortTile);
-    uint32_t *status0 = at<uint32_t>(ws, L.sort_status[0]);
+    // the first executed pass reads the survivors' buffer and its status
+    uint32_t *status0 = at<uint32_t>(ws, L.sort_status[ctrl->sort_in]);
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w = gtid; w < ntiles * 256; w += gthreads) status0[w] = 0u;
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
     __shared__ bool s_last;
     for (int i = threadIdx.x; i < kSortPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
     __syncthreads();
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[ctrl->sort_in]);
     const int64_t nq = (int64_t)s / 4;   // 16-byte vector loads
     const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
     for (int64_t i = gtid; i < nq; i += gthreads) {
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
         if (__ldcg(&(&ctrl->hist[0][0])[i]) == s) s_skip[i / 256] = 1;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t cur = 0;
+        uint32_t cur = ctrl->sort_in;
         for (int p = 0; p < kSortPasses; ++p) {
             ctrl->pass_skip[p] = s_skip[p];
             ctrl->pass_src[p] = cur;
