@@ -88,7 +88,8 @@ struct KgonCtrl {                         // zeroed with the control block
 };
 
 struct Kgon {                             // strictly convex, counter-clockwise; m < 3: unusable
-    uint32_t m, pad;
+    uint32_t m;
+    float cx, cy, r2;                     // quick-accept circle (r2 = 0: none)
     float vx[kKgonDirs], vy[kKgonDirs];
 };
 

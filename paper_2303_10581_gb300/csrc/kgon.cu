@@ -39,7 +39,7 @@ constexpr int KITEMS = 16;              // survivors per thread per tile
 constexpr int KTILE = KT * KITEMS;      // 4096
 constexpr int KNW = KT / 32;
 constexpr uint32_t kKgonMinS = 1u << 16;   // fewer survivors: not worth a pass
-constexpr int kSampleLog2 = 20;            // about 2^20 sample points
+constexpr int kSampleLog2 = 16;            // about 2^16 sample points
 
 __device__ __forceinline__ float2 survivor(const uint32_t *keys, const unsigned long long *pay, int64_t q)
 {
@@ -51,9 +51,13 @@ __device__ __forceinline__ bool left_strict(float ax, float ay, float bx, float 
     return orient(ax, ay, bx, by, p.x, p.y) > 0;
 }
 
-// Exact test; g in shared memory.
+// Exact test; g in shared memory.  Points strictly inside the polygon's
+// inscribed circle around (cx, cy) -- radius shrunk so that binary32
+// rounding of the squared distance cannot cross it -- are accepted at once.
 __device__ __forceinline__ bool kgon_inside(const Kgon &g, float2 p)
 {
+    const float dx = p.x - g.cx, dy = p.y - g.cy;
+    if (__fmaf_rn(dx, dx, dy * dy) < g.r2) return true;
     const int m = (int)g.m;
     if (!left_strict(g.vx[0], g.vy[0], g.vx[1], g.vy[1], p)) return false;
     if (!left_strict(g.vx[m - 1], g.vy[m - 1], g.vx[0], g.vy[0], p)) return false;
@@ -102,45 +106,45 @@ __global__ void __launch_bounds__(KT) kgon_extremes_kernel(void *ws, Layout L)
     __syncthreads();
     const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
     const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    const uint32_t lane = lane_id();
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const int64_t stride = std::max<int64_t>(1, (int64_t)s >> kSampleLog2);
     const int64_t nsamp = ((int64_t)s + stride - 1) / stride;
-    constexpr int PER = kKgonDirs / 32;   // directions owned by each lane
-    float best[PER];
+    constexpr int PER = kKgonDirs / 32;   // lane owns directions lane + 32 k
+    float best[PER], dc[PER], ds[PER];
     uint32_t bpos[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         best[k] = -__int_as_float(0x7f800000);
         bpos[k] = 0xffffffffu;
+        dc[k] = s_c[lane + 32 * k];
+        ds[k] = s_s[lane + 32 * k];
     }
+    // each warp stages 32 sample points; every lane scans them for its directions
+    __shared__ float2 s_p[KNW][32];
+    __shared__ uint32_t s_q[KNW][32];
     const int64_t wid = ((int64_t)blockIdx.x * KT + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * KT) >> 5;
     for (int64_t g0 = wid * 32; g0 < nsamp; g0 += nw * 32) {
         const int64_t k = g0 + lane;
         const bool ok = k < nsamp;
-        const uint32_t q = ok ? (uint32_t)(k * stride) : 0u;
-        const float2 p = ok ? survivor(keys, pay, q) : make_float2(0.0f, 0.0f);
-#pragma unroll 4
-        for (int j = 0; j < kKgonDirs; ++j) {
-            float v = ok ? __fmaf_rn(p.x, s_c[j], p.y * s_s[j]) : -__int_as_float(0x7f800000);
-            uint32_t pos = ok ? q : 0xffffffffu;
+        const uint32_t q = ok ? (uint32_t)(k * stride) : 0xffffffffu;
+        s_p[warp][lane] = ok ? survivor(keys, pay, q) : make_float2(0.0f, 0.0f);
+        s_q[warp][lane] = q;
+        __syncwarp();
+        const int cnt = (int)min((int64_t)32, nsamp - g0);
+        for (int i = 0; i < cnt; ++i) {
+            const float2 p = s_p[warp][i];
+            const uint32_t pq = s_q[warp][i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const uint32_t p2 = __shfl_xor_sync(0xffffffffu, pos, o);
-                if (v2 > v || (v2 == v && p2 < pos)) {
-                    v = v2;
-                    pos = p2;
-                }
-            }
-            if ((uint32_t)(j & 31) == lane) {
-                const int kk = j >> 5;
-                if (v > best[kk] || (v == best[kk] && pos < bpos[kk])) {
+            for (int kk = 0; kk < PER; ++kk) {
+                const float v = __fmaf_rn(p.x, dc[kk], p.y * ds[kk]);
+                if (v > best[kk]) {   // sample positions increase: ties keep the first
                     best[kk] = v;
-                    bpos[kk] = pos;
+                    bpos[kk] = pq;
                 }
             }
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k)
@@ -148,69 +152,154 @@ __global__ void __launch_bounds__(KT) kgon_extremes_kernel(void *ws, Layout L)
             atomicMax(&kc->slot[k * 32 + lane], ((unsigned long long)ord_key(best[k]) << 32) | (uint32_t)~bpos[k]);
 }
 
-// One warp.  Lane 0 runs Andrew's monotone chain over the (at most 128)
-// vertices -- exact orientation, strict turns -- so the polygon is strictly
-// convex and counter-clockwise whatever the sample gave.
+// One warp: the exact convex hull of the slots' points.  They are sorted by
+// (x, y) (each lane ranks its slots against all), duplicates dropped, and
+// the lower and the upper chain found by strict-turn elimination passes
+// over the sorted sequence -- a sequence whose every turn is strict is its
+// own chain, so this gives Andrew's chains (exact orientation) in parallel.
+// The polygon is strictly convex and counter-clockwise.
+__device__ __forceinline__ int warp_chain_pass(const float *px, const float *py, const uint8_t *src, uint8_t *dst,
+                                               int len, int side, uint32_t lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    int kept = 0;
+    for (int c0 = 0; c0 < len; c0 += 32) {
+        const int j = c0 + (int)lane;
+        bool k = j < len;
+        if (k && j > 0 && j < len - 1) {
+            const int a = src[j - 1], b = src[j], c = src[j + 1];
+            const int o = orient(px[a], py[a], px[b], py[b], px[c], py[c]);
+            k = side == 0 ? o > 0 : o < 0;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, k);
+        if (k) dst[kept + __popc(m & lt)] = src[j];
+        kept += __popc(m);
+    }
+    __syncwarp();
+    return kept;
+}
+
 __global__ void __launch_bounds__(32) kgon_build_kernel(void *ws, Layout L)
 {
-    __shared__ float px[kKgonDirs], py[kKgonDirs];
-    __shared__ int hx[2 * kKgonDirs + 2];
+    constexpr int K = kKgonDirs;
+    __shared__ float px[K], py[K];
+    __shared__ uint8_t sorted[K];
+    __shared__ uint8_t seq[2][2][K];   // [side][ping-pong]
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     Kgon *g = at<Kgon>(ws, L.kgon);
+    const uint32_t lane = lane_id();
     uint32_t s;
     if (!kgon_live(ctrl, at<Octagon>(ws, L.oct), s)) {
-        if (threadIdx.x == 0) g->m = 0;
+        if (lane == 0) {
+            g->m = 0;
+            g->r2 = 0.0f;
+        }
         return;
     }
     const KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
     const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    const uint32_t lane = lane_id();
-    for (int j = lane; j < kKgonDirs; j += 32) {
+    for (int j = lane; j < K; j += 32) {
         const unsigned long long v = kc->slot[j];
         const uint32_t pos = ~(uint32_t)v;
-        const float2 p = (v != 0ull && pos < s) ? survivor(keys, pay, pos) : survivor(keys, pay, 0);
+        const float2 p = survivor(keys, pay, (v != 0ull && pos < s) ? pos : 0u);
         px[j] = p.x;
         py[j] = p.y;
     }
     __syncwarp();
-    if (lane != 0) return;
-    // sort by (x, y): insertion sort of indices
-    int idx[kKgonDirs];
-    for (int j = 0; j < kKgonDirs; ++j) {
-        int k = j;
-        while (k > 0 && (px[idx[k - 1]] > px[j] || (px[idx[k - 1]] == px[j] && py[idx[k - 1]] > py[j]))) {
-            idx[k] = idx[k - 1];
-            --k;
+    // rank by (x, y, slot)
+    constexpr int PER = K / 32;
+    int r[PER];
+    float qx[PER], qy[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        r[k] = 0;
+        qx[k] = px[lane + 32 * k];
+        qy[k] = py[lane + 32 * k];
+    }
+    for (int i = 0; i < K; ++i) {
+        const float ix = px[i], iy = py[i];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int j = (int)lane + 32 * k;
+            r[k] += (ix < qx[k] || (ix == qx[k] && (iy < qy[k] || (iy == qy[k] && i < j)))) ? 1 : 0;
         }
-        idx[k] = j;
     }
-    // dedupe equal points
+#pragma unroll
+    for (int k = 0; k < PER; ++k) sorted[r[k]] = (uint8_t)(lane + 32 * k);
+    __syncwarp();
+    // drop equal points (keep the first of each run)
     int u = 0;
-    for (int j = 0; j < kKgonDirs; ++j)
-        if (u == 0 || px[idx[j]] != px[idx[u - 1]] || py[idx[j]] != py[idx[u - 1]]) idx[u++] = idx[j];
-    int h = 0;
-    for (int j = 0; j < u; ++j) {   // lower chain
-        while (h >= 2 && orient(px[hx[h - 2]], py[hx[h - 2]], px[hx[h - 1]], py[hx[h - 1]], px[idx[j]], py[idx[j]]) <= 0)
-            --h;
-        hx[h++] = idx[j];
+    for (int c0 = 0; c0 < K; c0 += 32) {
+        const int j = c0 + (int)lane;
+        const int a = sorted[j];
+        const bool k = j == 0 || px[sorted[j - 1]] != px[a] || py[sorted[j - 1]] != py[a];
+        const uint32_t m = __ballot_sync(0xffffffffu, k);
+        if (k) {
+            seq[0][0][u + __popc(m & ((1u << lane) - 1u))] = (uint8_t)a;
+            seq[1][0][u + __popc(m & ((1u << lane) - 1u))] = (uint8_t)a;
+        }
+        u += __popc(m);
     }
-    const int lower = h;
-    for (int j = u - 2; j >= 0; --j) {   // upper chain
-        while (h > lower && orient(px[hx[h - 2]], py[hx[h - 2]], px[hx[h - 1]], py[hx[h - 1]], px[idx[j]], py[idx[j]]) <= 0)
-            --h;
-        hx[h++] = idx[j];
+    __syncwarp();
+    int len[2] = {u, u}, cur[2] = {0, 0};
+    for (int side = 0; side < 2; ++side) {
+        for (int pass = 0; pass < K && len[side] > 2; ++pass) {
+            const int kept = warp_chain_pass(px, py, seq[side][cur[side]], seq[side][cur[side] ^ 1], len[side], side, lane);
+            cur[side] ^= 1;
+            const bool done = kept == len[side];
+            len[side] = kept;
+            if (done) break;
+        }
     }
-    const int m = h - 1;   // the first point closes the cycle
+    const int m = len[0] + len[1] - 2;
     if (u < 3 || m < 3) {
-        g->m = 0;
+        if (lane == 0) {
+            g->m = 0;
+            g->r2 = 0.0f;
+        }
         return;
     }
-    for (int j = 0; j < m; ++j) {
-        g->vx[j] = px[hx[j]];
-        g->vy[j] = py[hx[j]];
+    // counter-clockwise: the lower chain left to right, then the upper chain
+    // right to left without its two ends (shared with the lower one)
+    const uint8_t *lo = seq[0][cur[0]], *up = seq[1][cur[1]];
+    float sx = 0.0f, sy = 0.0f;
+    for (int j = lane; j < m; j += 32) {
+        const int a = j < len[0] ? lo[j] : up[len[1] - 2 - (j - len[0])];
+        g->vx[j] = px[a];
+        g->vy[j] = py[a];
+        sx += px[a];
+        sy += py[a];
     }
-    g->m = (uint32_t)m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    __syncwarp();   // the vertices in g are re-read below
+    // quick-accept circle around the vertex centroid c: a lower bound of
+    // c's distance to every edge line, from binary32 terms with a margin
+    // of 1e-5 of their magnitudes (far above their rounding errors); zero
+    // when c is not provably strictly inside
+    const float cx = sx / (float)m, cy = sy / (float)m;
+    float rmin = __int_as_float(0x7f800000);
+    for (int j = lane; j < m; j += 32) {
+        const int jn = j + 1 < m ? j + 1 : 0;
+        const float ax = g->vx[j], ay = g->vy[j], ex = g->vx[jn] - ax, ey = g->vy[jn] - ay;
+        const float t1 = ex * (cy - ay), t2 = ey * (cx - ax);
+        const float cr = (t1 - t2) - 1e-5f * (fabsf(t1) + fabsf(t2));
+        const float len_e = sqrtf(ex * ex + ey * ey) * (1.0f + 1e-5f);
+        const float d = len_e > 0.0f ? cr / len_e : -1.0f;
+        rmin = fminf(rmin, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    if (lane == 0) {
+        g->cx = cx;
+        g->cy = cy;
+        g->r2 = rmin > 0.0f && rmin < 1e18f ? rmin * rmin * (1.0f - 1e-4f) : 0.0f;
+        g->m = (uint32_t)m;
+    }
 }
 
 // Copies the polygon to shared memory; false when it is unusable.
@@ -218,7 +307,12 @@ __device__ __forceinline__ bool load_kgon(Kgon &sg, void *ws, const Layout &L)
 {
     const Kgon *g = at<Kgon>(ws, L.kgon);
     const uint32_t m = g->m;
-    if (threadIdx.x == 0) sg.m = m;
+    if (threadIdx.x == 0) {
+        sg.m = m;
+        sg.cx = g->cx;
+        sg.cy = g->cy;
+        sg.r2 = g->r2;
+    }
     for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
         sg.vx[j] = g->vx[j];
         sg.vy[j] = g->vy[j];
@@ -294,11 +388,38 @@ __global__ void __launch_bounds__(KT) kgon_count_kernel(void *ws, Layout L)
     uint32_t block_total = 0;
     for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
         const int64_t base = tile * KTILE;
-        uint32_t keep = 0;
-#pragma unroll 4
+        // all loads first (memory parallelism), then the quick test, then
+        // the full test for the few points outside the quick circle
+        float x[KITEMS], y[KITEMS];
+        uint32_t live = 0;
+#pragma unroll
         for (int r = 0; r < KITEMS; ++r) {
             const int64_t q = base + r * KT + threadIdx.x;
-            if (q < s && !kgon_inside(sg, survivor(keys, pay, q))) keep |= 1u << r;
+            x[r] = y[r] = 0.0f;
+            if (q < s) {
+                x[r] = key_float(__ldcs(keys + q));
+                y[r] = key_float(__ldcs(reinterpret_cast<const uint2 *>(pay) + q).y);
+                live |= 1u << r;
+            }
+        }
+        uint32_t keep = 0, slow = 0;
+#pragma unroll
+        for (int r = 0; r < KITEMS; ++r) {
+            const float dx = x[r] - sg.cx, dy = y[r] - sg.cy;
+            if (!(__fmaf_rn(dx, dx, dy * dy) < sg.r2)) slow |= 1u << r;
+        }
+        slow &= live;
+        while (slow) {
+            const int r = __ffs(slow) - 1;
+            slow &= slow - 1;
+            float xr = 0.0f, yr = 0.0f;
+#pragma unroll
+            for (int k = 0; k < KITEMS; ++k)
+                if (k == r) {
+                    xr = x[k];
+                    yr = y[k];
+                }
+            if (!kgon_inside(sg, make_float2(xr, yr))) keep |= 1u << r;
         }
         bits[tile * KT + threadIdx.x] = (uint16_t)keep;
         uint32_t c = __popc(keep);
