@@ -370,6 +370,9 @@ __global__ void __launch_bounds__(KT) kgon_count_kernel(void *ws, Layout L)
 {
     __shared__ Kgon sg;
     __shared__ uint32_t s_w[KNW];
+    __shared__ float2 s_qp[KNW][64];
+    __shared__ uint16_t s_tag[KNW][64];
+    __shared__ uint32_t s_res[KNW][32];
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     uint32_t s;
     if (!kgon_live(ctrl, at<Octagon>(ws, L.oct), s)) return;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(KT) kgon_count_kernel(void *ws, Layout L)
     const int64_t ntiles = ceil_div((int64_t)s, KTILE);
     const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
     const int64_t t1 = std::min<int64_t>(ntiles, (int64_t)(blockIdx.x + 1) * per);
-    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id(), lt = (1u << lane) - 1u;
     uint32_t block_total = 0;
     for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
         const int64_t base = tile * KTILE;
@@ -397,29 +400,63 @@ __global__ void __launch_bounds__(KT) kgon_count_kernel(void *ws, Layout L)
             const int64_t q = base + r * KT + threadIdx.x;
             x[r] = y[r] = 0.0f;
             if (q < s) {
-                x[r] = key_float(__ldcs(keys + q));
-                y[r] = key_float(__ldcs(reinterpret_cast<const uint2 *>(pay) + q).y);
+                x[r] = key_float(__ldg(keys + q));
+                y[r] = key_float(__ldg(reinterpret_cast<const uint2 *>(pay) + q).y);
                 live |= 1u << r;
             }
         }
-        uint32_t keep = 0, slow = 0;
+        uint32_t slow = 0;
 #pragma unroll
         for (int r = 0; r < KITEMS; ++r) {
             const float dx = x[r] - sg.cx, dy = y[r] - sg.cy;
             if (!(__fmaf_rn(dx, dx, dy * dy) < sg.r2)) slow |= 1u << r;
         }
         slow &= live;
-        while (slow) {
-            const int r = __ffs(slow) - 1;
-            slow &= slow - 1;
-            float xr = 0.0f, yr = 0.0f;
+        // points outside the quick circle: queued per warp with their
+        // coordinates and tested 32 at a time by all lanes as the queue
+        // fills (kept bits come back per owner lane)
+        uint32_t keep = 0;
+        if (__any_sync(0xffffffffu, slow != 0u)) {
+            s_res[warp][lane] = 0u;
+            int cnt = 0;
 #pragma unroll
-            for (int k = 0; k < KITEMS; ++k)
-                if (k == r) {
-                    xr = x[k];
-                    yr = y[k];
+            for (int r = 0; r < KITEMS; ++r) {
+                const bool b = (slow >> r) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, b);
+                if (m == 0u) continue;
+                if (b) {
+                    const int at_ = cnt + __popc(m & lt);
+                    s_qp[warp][at_] = make_float2(x[r], y[r]);
+                    s_tag[warp][at_] = (uint16_t)((lane << 4) | (uint32_t)r);
                 }
-            if (!kgon_inside(sg, make_float2(xr, yr))) keep |= 1u << r;
+                cnt += __popc(m);
+                if (cnt >= 32) {   // a full round; the overflow moves to the front
+                    __syncwarp();
+                    const uint32_t tg = s_tag[warp][lane];
+                    if (!kgon_inside(sg, s_qp[warp][lane])) atomicOr(&s_res[warp][tg >> 4], 1u << (tg & 15u));
+                    const bool more = (int)lane + 32 < cnt;
+                    float2 pv = make_float2(0.0f, 0.0f);
+                    uint16_t tv = 0;
+                    if (more) {
+                        pv = s_qp[warp][lane + 32];
+                        tv = s_tag[warp][lane + 32];
+                    }
+                    __syncwarp();
+                    if (more) {
+                        s_qp[warp][lane] = pv;
+                        s_tag[warp][lane] = tv;
+                    }
+                    cnt -= 32;
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+            if ((int)lane < cnt) {
+                const uint32_t tg = s_tag[warp][lane];
+                if (!kgon_inside(sg, s_qp[warp][lane])) atomicOr(&s_res[warp][tg >> 4], 1u << (tg & 15u));
+            }
+            __syncwarp();
+            keep = s_res[warp][lane];
         }
         bits[tile * KT + threadIdx.x] = (uint16_t)keep;
         uint32_t c = __popc(keep);
