@@ -201,3 +201,42 @@ def test_parity_single_pass_variant(dist, n):
 def test_filter_variant_rejects_unknown():
     with pytest.raises(ch.CHError):
         ch.ch_filter_variant(7)
+
+
+def _kgon_case(case, rng):
+    if case == "displaced_ellipse":
+        p = pointgen.make_points("displaced", 300_000, seed=41).astype(np.float64)
+        p[:, 0] *= 10.0
+        return p.astype(np.float32)
+    if case == "ring_outliers":
+        p = pointgen.make_points("displaced", 250_000, seed=42)
+        far = (rng.standard_normal((50, 2)) * 3).astype(np.float32)
+        return np.concatenate([p, far])
+    if case == "collinear_big":
+        t = rng.uniform(-5, 5, 200_000).astype(np.float32)
+        return np.stack([t, np.float32(3) * t + np.float32(1)], 1)
+    if case == "duplicated_ring":
+        base = pointgen.make_points("displaced", 5_000, seed=43)
+        return base[rng.integers(0, 5_000, 300_000)]
+    if case == "square_boundary":
+        t = rng.uniform(-1, 1, 300_000).astype(np.float32)
+        side = rng.integers(0, 4, 300_000)
+        one = np.ones_like(t)
+        x = np.where(side == 0, one, np.where(side == 1, -one, t))
+        y = np.where(side == 2, one, np.where(side == 3, -one, t))
+        return np.stack([x, y], 1).astype(np.float32)
+    if case == "tiny_scale":
+        return (pointgen.make_points("displaced", 200_000, seed=44) * np.float32(1e-30)).astype(np.float32)
+    if case == "huge_scale":
+        return (pointgen.make_points("displaced", 200_000, seed=45) * np.float32(1e30)).astype(np.float32)
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["displaced_ellipse", "ring_outliers", "collinear_big", "duplicated_ring",
+                                  "square_boundary", "tiny_scale", "huge_scale"])
+def test_second_polygon_cases(case):
+    """Inputs with at least 2^16 survivors, so the hull step's second polygon
+    (sample extremes along many directions) is built and, where it removes
+    enough, applied -- including degenerate polygons and extreme scales."""
+    p = _kgon_case(case, np.random.default_rng(7))
+    check_against_oracle(p)
