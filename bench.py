@@ -146,22 +146,27 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline bookkeeping
 
-def algorithmic_bytes(kernel, n, s_list):
+def algorithmic_bytes(kernel, n, s_list, t_list):
     """Bytes a kernel must move in one step (all its launches for the step's
     sets), from the data it reads and writes by definition; s_list holds the
-    survivor count of each set."""
+    octagon-filter survivors of each set, t_list the points the hull step
+    sorts (after its second polygon)."""
     if kernel == "extremes":
         return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
-        return sum(8 * n + 12 * s for s in s_list)          # read points, write key + index per survivor
+        return sum(8 * n + 12 * s for s in s_list)          # read points, write key + payload per survivor
+    if kernel == "kgon":
+        # the pass over all survivors when it ran (read key + payload, write
+        # the kept ones); otherwise only the samples
+        return sum(12 * s + 12 * t if t < s else 0 for s, t in zip(s_list, t_list))
     if kernel == "sort_hist":
-        return sum(4 * s for s in s_list)                   # read the 32-bit keys
+        return sum(4 * t for t in t_list)                   # read the 32-bit keys
     if kernel == "sort_pass":
-        # 4 passes (32-bit x key) per set with more than one survivor; each
-        # reads and writes key (4 B) + payload (8 B): 24 B per survivor
-        return sum(4 * 24 * s for s in s_list if s > 1)
+        # 4 passes (32-bit x key) per set with more than one point; each
+        # reads and writes key (4 B) + payload (8 B): 24 B per point
+        return sum(4 * 24 * t for t in t_list if t > 1)
     if kernel == "chain":
-        return sum(12 * s for s in s_list)                  # read the sorted keys and payloads once
+        return sum(12 * t for t in t_list)                  # read the sorted keys and payloads once
     return None
 
 
@@ -271,24 +276,21 @@ def run_ours(args):
     # one probed step, set by set: event time of every kernel
     per_set = {}
     probe_all = {k: (0.0, 0) for k in KERNEL_IDS}
+    surv, sorted_pts = [], []
     for k in range(len(DISTS)):
         ch.ch_probe_start(KERNEL_IDS, max_launches=64)
         ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
         pr = ch.ch_probe_stop()
         per_set[DISTS[k]] = {kk: round(v[0], 4) for kk, v in pr.items() if v[1]}
         probe_all = {kk: (probe_all[kk][0] + pr[kk][0], probe_all[kk][1] + pr[kk][1]) for kk in KERNEL_IDS}
+        c = ch.ch_hull_counts(ws.buf, n, stream)
+        surv.append(c[0])
+        sorted_pts.append(c[1])
     ws.check()
     dominant = max(probe_all, key=lambda k: probe_all[k][0])
     total_probe = sum(v[0] for v in probe_all.values())
     shares = {k: round(v[0] / total_probe, 4) for k, v in probe_all.items() if v[1]}
     hull_sizes = [int(c.item()) for c in hull_cnt]
-    # survivor counts: ask the filter directly (same polygon, same result)
-    surv = []
-    for k in range(len(DISTS)):
-        e = ch.extremes(d_pts[k], ws)
-        _, _, cnt = ch.filter_points(d_pts[k], e, ws, with_points=False)
-        surv.append(int(cnt.item()))
-    ws.check()
 
     # timed region: the dominant kernel's launches are event-timed on the stream
     clocks = ClockSampler(local)
@@ -317,7 +319,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     roof = None
     if dom_launches:
-        per_step_bytes = algorithmic_bytes(dominant, n, surv)
+        per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts)
         if per_step_bytes is not None:
             # algorithmic bytes of all timed launches over their summed event
             # time (= per-launch bytes over the average launch duration)
@@ -335,7 +337,7 @@ def run_ours(args):
     filt = None
     if probe_all["filter"][1]:
         fms = probe_all["filter"][0]
-        fb = algorithmic_bytes("filter", n, surv)
+        fb = algorithmic_bytes("filter", n, surv, sorted_pts)
         filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / len(DISTS), 4),
                 "gbs": round(fb / (fms * 1e-3) / 1e9, 1), "frac_of_peak": round(fb / (fms * 1e-3) / 1e9 / peak, 4)}
 
@@ -386,7 +388,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+exact", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_per_set": n, "sets_per_step": len(DISTS),
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
-                       "survivors": dict(zip(DISTS, surv)), "hull_sizes": dict(zip(DISTS, hull_sizes))},
+                       "survivors": dict(zip(DISTS, surv)), "sorted": dict(zip(DISTS, sorted_pts)),
+                       "hull_sizes": dict(zip(DISTS, hull_sizes))},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roof, "filter": filt, "kernel_shares": shares, "kernel_ms_per_set": per_set,
             "hull_ms_per_set": {d: round(sum(v.values()), 4) for d, v in per_set.items()},

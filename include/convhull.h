@@ -172,6 +172,13 @@ typedef enum {
  * the events. */
 ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
 
+/* After a ch_hull call for n points on ws has completed (waits for
+ * `stream`): counts[0] = points that survived the octagon filter,
+ * counts[1] = points the hull step sorted (fewer when its second polygon,
+ * built from extreme survivors along more directions, removed some).
+ * Instrumentation; CH_ERR_ARG / CH_ERR_CAPACITY as for ch_hull. */
+ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32_t *counts, void *stream);
+
 /* Stop timing: waits for the recorded events, writes per kernel id the summed
  * event-measured milliseconds (ms[CH_K_COUNT], 0 when not timed) and the
  * number of kernels launched under it since ch_probe_start, in every

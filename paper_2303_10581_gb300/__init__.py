@@ -32,7 +32,7 @@ CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOU
 
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
-           "ch_filter_variant")
+           "ch_filter_variant", "ch_hull_counts")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
     lib.ch_probe_stop.argtypes = [p, p]
     lib.ch_filter_noalloc.argtypes = [p, i64, p, p, p, p, p]
     lib.ch_filter_variant.argtypes = [ctypes.c_int32]
+    lib.ch_hull_counts.argtypes = [p, sz, i64, p, p]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -144,6 +145,15 @@ def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):
     _check(load().ch_hull_batched(_ptr(pts, "pts"), _ptr(offsets, "offsets"), offsets.shape[0] - 1,
                                   _ptr(hull_idx, "hull_idx"), _ptr(hull_offsets, "hull_offsets"),
                                   _ptr(ws, "ws"), ws.numel(), _stream(stream)), "ch_hull_batched")
+
+
+def ch_hull_counts(ws, n, stream=None):
+    """(octagon survivors, points sorted) of the last ch_hull call for n
+    points on ws (instrumentation; synchronises the stream)."""
+    out = (ctypes.c_uint32 * 2)()
+    _check(load().ch_hull_counts(_ptr(ws, "ws"), ws.numel(), int(n), ctypes.addressof(out), _stream(stream)),
+           "ch_hull_counts")
+    return int(out[0]), int(out[1])
 
 
 def ch_last_error(ws, stream=None) -> int:

@@ -125,6 +125,22 @@ extern "C" ch_status ch_hull_batched(const float *pts, const int64_t *offsets, i
     return cuda_status(e);
 }
 
+extern "C" ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32_t *counts, void *stream)
+{
+    if (!counts || n < 1) return CH_ERR_ARG;
+    if (n >= kMaxHullN) return CH_ERR_CAPACITY;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return CH_ERR_CUDA;
+    uint32_t sorted = 0, s_in = 0;
+    if (cudaMemcpy(&sorted, &at<Ctrl>(ws, L.ctrl)->surv_count, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&s_in, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_in, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CH_ERR_CUDA;
+    counts[0] = s_in ? s_in : sorted;
+    counts[1] = sorted;
+    return CH_OK;
+}
+
 extern "C" ch_status ch_last_error(void *ws, void *stream)
 {
     if (!ws || !aligned(ws, 256)) return CH_ERR_ARG;
