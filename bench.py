@@ -111,7 +111,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "25"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -216,7 +216,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    sample_n = 1_000_000
+    sample_n = 4_000_000
     for _ in range(args.warmup):
         cpu_oracle_rate(sample_n // 10, args.seed)
     times = []
@@ -376,7 +376,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample_n = 1_000_000
+        sample_n = 20_000_000   # about 10 s of single-core oracle work
         rate, dt = cpu_oracle_rate(sample_n, args.seed)
         cpu = {"value": round(rate, 5), "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample_n} points of each distribution (3 sets), whole path, {dt:.1f} s"}
