@@ -22,24 +22,27 @@
 //     lies on or above a segment between two points of the set, so it is
 //     not a strict vertex of the lower hull and the sequential chain would
 //     pop it too; a sequence where every turn is strict is its own monotone
-//     chain.  Passes repeat until nothing changes or kElimPasses is
-//     reached; each is a compaction with a block scan.  On dense circles
-//     the first pass alone removes 70-99% of the points.
-//  2. leaf chains and merges: what is left is cut into leaves of 16; one
-//     thread runs the sequential monotone chain on each.  Chains are merged
-//     pairwise up a binary tree -- first inside the block over its 256
-//     leaves (shared memory, one level per barrier), then across
-//     super-chunks in global memory by a second kernel, where the second
-//     child to finish merges the pair (no thread ever waits).  Two
-//     x-ordered lower chains A | B merge by walking the common tangent: the
-//     cursor b on B moves right while B's next vertex is on or below
-//     line(a, b); the cursor a on A moves left while A's previous vertex is
-//     on or below line(a, b); repeat until neither moves.  The merged chain
-//     is A up to a followed by B from b, which is what the sequential chain
-//     produces (same pops, same collinear exclusion).  Each chunk keeps the
-//     surviving range [lo, hi] of its chain; chunks whose range empties are
-//     unlinked from a list of live chunks.  Upper chains are handled the
-//     same way with the predicate mirrored.
+//     chain.  Each warp first runs passes over its share of the sequence
+//     (its two ends stay); then the warps' survivors are concatenated and
+//     the passes continue over the whole super-chunk sequence (block-wide
+//     while long, one warp once short) until nothing changes.  The
+//     converged sequence is written out as the super-chunk's chain.
+//  2. fallback, when the passes do not converge within their cap: what is
+//     left is cut into leaves; one thread runs the sequential monotone
+//     chain on each, and the leaf chains are merged pairwise up a binary
+//     tree inside the block (shared memory, one level per barrier).
+//     Across super-chunks a second kernel merges the chains up a tree in
+//     global memory, where the second child to finish merges the pair (no
+//     thread ever waits).  Two x-ordered lower chains A | B merge by walking
+//     the common tangent: the cursor b on B moves right while B's next
+//     vertex is on or below line(a, b); the cursor a on A moves left while
+//     A's previous vertex is on or below line(a, b); repeat until neither
+//     moves.  The merged chain is A up to a followed by B from b, which is
+//     what the sequential chain produces (same pops, same collinear
+//     exclusion).  Each chunk keeps the surviving range [lo, hi] of its
+//     chain; chunks whose range empties are unlinked from a list of live
+//     chunks.  Upper chains are handled the same way with the predicate
+//     mirrored.
 //  3. emit: one pass compacts the live ranges (decoupled look-back over
 //     super-chunk counts) into the lower chain and the upper chain, and the
 //     final kernel appends the upper chain, reversed and without its end

@@ -7,17 +7,24 @@
 // variants are built:
 //
 //  * two-pass (default): a streaming count pass tests 4096-point tiles and
-//    writes one survivor count per tile; one block scans the counts into
-//    tile offsets; a scatter pass revisits only the tiles that have
-//    survivors, re-tests them (same arithmetic, same decisions) and writes
-//    the kept points in ascending index order.  No block waits on another,
-//    so every pass streams at memory speed; when almost everything is
-//    discarded (normal data) the points are read once, when nothing is
-//    (circle) they are read twice.
+//    writes keep bits and one survivor count per tile, each block over a
+//    contiguous range of tiles, plus the block's total; a scatter pass with
+//    the same grid finds each tile's output offset from the block totals
+//    and an in-block scan of its range, visits only the tiles that have
+//    survivors, loads only the kept points and writes them in ascending
+//    index order.  No block waits on another, so both passes stream at
+//    memory speed; when almost everything is discarded (normal data) the
+//    points are read once, when nothing is (circle) they are read twice.
 //  * single-pass: one persistent kernel takes tiles in ticket order, tests
 //    them, publishes the tile count, gets its offset by decoupled look-back
 //    and writes its survivors; points are read once, but each tile waits on
 //    its predecessors.
+//
+// The test: the quick-discard rectangle, then the polygon edge facing the
+// point's octant; a point strictly left of that edge is likely inside and
+// needs every edge, so such points are queued per warp and tested 32 at a
+// time (spread over the lanes they would hold whole warps in the edge
+// loop).
 //
 // Memory traffic: 8 bytes per point read (twice for tiles with survivors in
 // the two-pass variant), 12 bytes per kept point written.

@@ -20,6 +20,10 @@
 // digit-sorted, so stores are runs of consecutive addresses.  The payload
 // is staged in shared memory in element order and gathered through the
 // tile's inverse permutation at write-out, so it never occupies registers.
+// When a block takes a ticket it also asks the TMA unit to bring the tile
+// one grid ahead into L2 (tickets go out in order, so that tile is taken
+// about one tile-time later).  The survivors come from the buffer the hull
+// step left them in (ctrl->sort_in: 0, or 1 after its second polygon).
 #include <algorithm>
 
 #include "common.cuh"
