@@ -348,10 +348,28 @@ def run_ours(args):
         out_host = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in DISTS]
         cnt_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in DISTS]
 
+        # copies and hulls overlap: every set's points go up on two copy
+        # streams (halves) while the compute stream works on the previous
+        # set; the set with the shortest hull goes last
+        copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+        order = sorted(range(len(DISTS)), key=lambda k: -sum(per_set[DISTS[k]].values()))
+        half = n // 2
+
         def e2e_step():
             d2h = 0
-            for k in range(len(DISTS)):
-                d_pts[k].copy_(pinned[k], non_blocking=True)
+            ready = []
+            for k in order:
+                evs = []
+                for c, (lo, hi) in enumerate(((0, half), (half, n))):
+                    with torch.cuda.stream(copy_streams[c]):
+                        d_pts[k][lo:hi].copy_(pinned[k][lo:hi], non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(copy_streams[c])
+                        evs.append(ev)
+                ready.append(evs)
+            for k, evs in zip(order, ready):
+                for ev in evs:
+                    stream.wait_event(ev)
                 ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
                 cnt_host[k].copy_(hull_cnt[k], non_blocking=True)
             stream.synchronize()
