@@ -393,6 +393,11 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
     const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
     uint32_t block_total = 0;
     for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
+        if (threadIdx.x == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const int64_t nb = (tile + 1) * kFiltTile;
+            const uint32_t nn = (uint32_t)std::min<int64_t>(kFiltTile, n - nb);
+            if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
+        }
         float px[kFiltItems], py[kFiltItems];
         const uint32_t keep = load_test<G>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
         bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;

@@ -391,6 +391,11 @@ __global__ void __launch_bounds__(KT) kgon_count_kernel(void *ws, Layout L)
     uint32_t block_total = 0;
     for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
         const int64_t base = tile * KTILE;
+        if (threadIdx.x == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const uint32_t nn = (uint32_t)std::min<int64_t>(KTILE, (int64_t)s - base - KTILE);
+            bulk_prefetch_l2(keys + base + KTILE, (nn * 4u) & ~15u);
+            bulk_prefetch_l2(pay + base + KTILE, (nn * 8u) & ~15u);
+        }
         // all loads first (memory parallelism), then the quick test, then
         // the full test for the few points outside the quick circle
         float x[KITEMS], y[KITEMS];
