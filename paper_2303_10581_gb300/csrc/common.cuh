@@ -77,20 +77,22 @@ struct ExtCtrl {
     uint32_t nonfinite;               // a non-finite coordinate was seen
 };
 
-// second throw-away polygon of the hull step (kgon.cu)
-constexpr int kKgonDirs = 128;
+// second throw-away step of the hull step (kgon.cu): a fan of triangles
+// around the bounding-box centre, one vertex per angular bin
+constexpr int kFanBins = 16384;
 
-struct KgonCtrl {                         // zeroed with the control block
-    unsigned long long slot[kKgonDirs];   // packed (ord(dot) << 32 | ~position) per direction
-    uint32_t sample, inside;              // the estimate's sample and how much of it is inside
-    uint32_t s_in;                        // survivors entering the pass (0: the pass did not run)
+struct KgonCtrl {                          // zeroed with the control block
+    unsigned long long slot[kFanBins];     // packed (r^2 bits << 32 | ~position): farthest sampled survivor per bin
+    uint32_t sample, inside;               // the estimate's sample and how much of it is inside
+    uint32_t s_in;                         // survivors entering the pass (0: the pass did not run)
     uint32_t pad;
 };
 
-struct Kgon {                             // strictly convex, counter-clockwise; m < 3: unusable
-    uint32_t m;
-    float cx, cy, r2;                     // quick-accept circle (r2 = 0: none)
-    float vx[kKgonDirs], vy[kKgonDirs];
+struct Kgon {
+    float cx, cy;                          // fan centre, strictly inside the hull
+    uint32_t ok;                           // 0: no fan this call
+    uint32_t pad;
+    float2 v[kFanBins];                    // vertex of every bin (input points)
 };
 
 // control block: zeroed at the start of every call (together with the
@@ -121,8 +123,8 @@ struct Persist {
 struct Layout {
     size_t persist, extctrl, oct, ext8;
     size_t ctrl;            // Ctrl, immediately followed by
-    size_t kgon_ctrl;       // KgonCtrl,
     size_t filt_status;     // u64[filt_tiles],
+    size_t kgon_ctrl;       // KgonCtrl,
     size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node, and
     size_t emit_status[2];  // u64[emit_tiles]: look-back of the chain compaction
     size_t zero_words;      // u64 words from ctrl to the end of emit_status[1]
@@ -228,8 +230,8 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.oct = take(sizeof(Octagon));
     L.ext8 = take(8 * sizeof(uint32_t));
     L.ctrl = take(sizeof(Ctrl));
-    L.kgon_ctrl = take(sizeof(KgonCtrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
+    L.kgon_ctrl = take(sizeof(KgonCtrl));
     L.node_cnt = take((size_t)L.n_nodes * 4);
     L.emit_status[0] = take((size_t)L.emit_tiles * 8);
     L.emit_status[1] = take((size_t)L.emit_tiles * 8);
