@@ -150,15 +150,15 @@ def algorithmic_bytes(kernel, n, s_list, t_list):
     """Bytes a kernel must move in one step (all its launches for the step's
     sets), from the data it reads and writes by definition; s_list holds the
     octagon-filter survivors of each set, t_list the points the hull step
-    sorts (after its second polygon)."""
+    sorts (the survivors of the fan test as well, when it ran)."""
     if kernel == "extremes":
         return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
-        return sum(8 * n + 12 * s for s in s_list)          # read points, write key + payload per survivor
+        return sum(8 * n + 12 * t for t in t_list)          # read points, write key + payload per point kept
     if kernel == "kgon":
-        # the pass over all survivors when it ran (read key + payload, write
-        # the kept ones); otherwise only the samples
-        return sum(12 * s + 12 * t if t < s else 0 for s, t in zip(s_list, t_list))
+        # the fan test of the octagon survivors when it ran (read their
+        # coordinates); otherwise only samples
+        return sum(8 * s if t < s else 0 for s, t in zip(s_list, t_list))
     if kernel == "sort_hist":
         return sum(4 * t for t in t_list)                   # read the 32-bit keys
     if kernel == "sort_pass":

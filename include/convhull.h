@@ -155,8 +155,8 @@ typedef enum {
     CH_K_CHAIN = 5,      /* Sec. 3.3 chunk chains + tree merges                 */
     CH_K_EMIT = 6,       /* compaction of the chain ranges                      */
     CH_K_FINISH = 7,     /* hull assembly                                       */
-    CH_K_KGON = 8,       /* hull step: second polygon over the survivors
-                            (runs after FILTER, before SORT_HIST)             */
+    CH_K_KGON = 8,       /* hull step: fan test of the octagon survivors
+                            (runs between FILTER's count and scatter passes) */
     CH_K_COUNT = 9
 } ch_kernel_id;
 
@@ -165,17 +165,18 @@ typedef enum {
  * launch stream, for at most max_launches groups per id.  A group is the
  * kernels one step launches back to back under that id: one for
  * EXTREMES, OCTAGON, SORT_HIST, SORT_PASS (one per pass), EMIT, FINISH;
- * two for FILTER with the two-pass schedule (count, scatter), one with the
- * single pass; two for CHAIN (chains, tree merge); five for KGON (sample
- * extremes, polygon, estimate, count, scatter).  Kernel-launch
+ * two for FILTER with the two-pass schedule (count, scatter; in ch_hull
+ * each is its own group, KGON runs between them), one with the single pass;
+ * two for CHAIN (chains, tree merge); four for KGON (bins, fan vertices,
+ * estimate, refine of the keep decisions).  Kernel-launch
  * counting for all ids restarts at zero.  Host-only bookkeeping; creates
  * the events. */
 ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
 
 /* After a ch_hull call for n points on ws has completed (waits for
  * `stream`): counts[0] = points that survived the octagon filter,
- * counts[1] = points the hull step sorted (fewer when its second polygon,
- * built from extreme survivors along more directions, removed some).
+ * counts[1] = points the hull step sorted (fewer when its fan of triangles
+ * around the bounding-box centre removed some).
  * Instrumentation; CH_ERR_ARG / CH_ERR_CAPACITY as for ch_hull. */
 ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32_t *counts, void *stream);
 

@@ -85,8 +85,7 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
                                     at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st);
-    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st);
-    if (e == cudaSuccess) e = launch_kgon(ws, L, st);
+    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, -1, true);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
     if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
     return cuda_status(e);
@@ -132,11 +131,11 @@ extern "C" ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32
     const Layout L = make_layout(n);
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return CH_ERR_CUDA;
-    uint32_t sorted = 0, s_in = 0;
+    uint32_t sorted = 0, s_oct = 0;
     if (cudaMemcpy(&sorted, &at<Ctrl>(ws, L.ctrl)->surv_count, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&s_in, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_in, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(&s_oct, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_oct, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CH_ERR_CUDA;
-    counts[0] = s_in ? s_in : sorted;
+    counts[0] = s_oct ? s_oct : sorted;
     counts[1] = sorted;
     return CH_OK;
 }

@@ -82,9 +82,9 @@ struct ExtCtrl {
 constexpr int kFanBins = 16384;
 
 struct KgonCtrl {                          // zeroed with the control block
-    unsigned long long slot[kFanBins];     // packed (r^2 bits << 32 | ~position): farthest sampled survivor per bin
-    uint32_t sample, inside;               // the estimate's sample and how much of it is inside
-    uint32_t s_in;                         // survivors entering the pass (0: the pass did not run)
+    unsigned long long slot[kFanBins];     // packed (r^2 bits << 32 | ~index): farthest sampled input point per bin
+    uint32_t sample, inside;               // the estimate's sample and how much of it is inside the fan
+    uint32_t s_oct;                        // octagon survivors (0: the fan kernels did not run)
     uint32_t pad;
 };
 
@@ -108,7 +108,7 @@ struct Ctrl {
     uint32_t hist_done;
     uint32_t emit_ticket[2];
     uint32_t h_lower, h_upper;
-    uint32_t sort_in;                 // buffer holding the survivors for the sort (0, or 1 after the polygon pass)
+    uint32_t sort_in;                 // buffer holding the survivors for the sort (the filter writes buffer 0)
     uint32_t pad;
 };
 

@@ -26,6 +26,10 @@
 // time (spread over the lanes they would hold whole warps in the edge
 // loop).
 //
+// In the hull step the fan test of kgon.cu runs between the two passes and
+// clears keep bits of points strictly inside the fan, so the scatter pass
+// writes only the points that survive both tests.
+//
 // Memory traffic: 8 bytes per point read (twice for tiles with survivors in
 // the two-pass variant), 12 bytes per kept point written.
 #include <algorithm>
@@ -802,7 +806,7 @@ cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L
 
 template <int G, bool KEYS>
 cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                            float *surv_pts, uint32_t *surv_count, cudaStream_t st)
+                            float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan)
 {
     static int per_sm_c = occupancy(filter_count_kernel<G>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
@@ -810,6 +814,12 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     const int64_t bc = std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
     filter_count_kernel<G><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    if (fan) {   // timed as its own group, between the filter's two
+        probe_after(CH_K_FILTER, st);
+        const cudaError_t e = launch_fan(pts, n, G == 2, bc, ws, L, st);
+        if (e != cudaSuccess) return e;
+        probe_before(CH_K_FILTER, st);
+    }
     filter_scatter_kernel<G, KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(
         pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
     note_kernels(CH_K_FILTER, 2);
@@ -820,12 +830,12 @@ int g_filter_variant = 0;   // 0: two passes, 1: single pass with look-back
 
 template <int G, bool KEYS>
 cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                           float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant)
+                           float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant, bool fan)
 {
     probe_before(CH_K_FILTER, st);
     const cudaError_t e = variant == 1
                               ? launch_single<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st)
-                              : launch_two_pass<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st);
+                              : launch_two_pass<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
     probe_after(CH_K_FILTER, st);
     return e;
 }
@@ -833,15 +843,16 @@ cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &
 }  // namespace
 
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant)
+                          float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant,
+                          bool fan)
 {
     const int v = variant < 0 ? g_filter_variant : variant;
     const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
     if (keys_mode)
-        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v)
-                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v);
-    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v)
-               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v);
+        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan)
+                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan);
+    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false)
+               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false);
 }
 
 cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)

@@ -1,34 +1,36 @@
 // kgon.cu -- a second throw-away step inside the device hull: a fan of
-// triangles around an interior point.
+// triangles around an interior point, applied to the octagon filter's keep
+// decisions before its survivors are written.
 //
 // The octagon filter (Sec. 3.1-3.2) removes almost nothing from points near
 // a circle, and on a displaced circle 95 % survive it, although the hulls
-// have a small fraction of the points as vertices.  Before sorting the
-// survivors the hull step repeats the throw-away idea of Sec. 3.1 on a much
-// finer scale.  Let c be the centre of the bounding box, checked with exact
-// signs to lie strictly inside the octagon, hence strictly inside the hull.
-// The plane around c is cut into kFanBins angular bins; the vertex of a bin
-// is the survivor farthest from c among a sample (every 4th 4096-point tile
-// of the survivors), and a bin the sample missed repeats the vertex before
-// it.  For consecutive vertices v, w every point strictly inside the
-// triangle (c, v, w) is a combination of c, v and w with positive weights,
-// so it lies strictly inside the hull and is no vertex of it: it is
-// dropped.  This holds whatever the vertices are (they are input points),
-// so nothing needs to be exact but the three orientation signs of the
-// final test, and a triangle that comes out clockwise or flat drops
-// nothing.
+// have a small fraction of the points as vertices.  The hull step repeats
+// the throw-away idea of Sec. 3.1 on a much finer scale.  Let c be the
+// centre of the bounding box, checked with exact signs to lie strictly
+// inside the octagon, hence strictly inside the hull.  The plane around c
+// is cut into kFanBins angular bins; the vertex of a bin is the input point
+// farthest from c among a sample (every 4th 4096-point tile of the input),
+// and a bin the sample missed repeats the vertex before it.  For
+// consecutive vertices v, w every point strictly inside the triangle
+// (c, v, w) is a combination of c, v and w with positive weights, so it
+// lies strictly inside the hull and is no vertex of it: it is dropped.
+// This holds whatever the vertices are (they are input points), so nothing
+// needs to be exact but the three orientation signs of the final test, and
+// a triangle that comes out clockwise or flat drops nothing.
 //
-//  kgon_bins_kernel      per bin, the farthest sampled survivor (atomicMax
-//                        of (r^2 bits << 32 | ~position), in shared memory
-//                        per block, then in global memory)
-//  kgon_build_kernel     exact centre check against the octagon; the vertex
-//                        of every bin
-//  kgon_estimate_kernel  exact test of a second sample: the pass runs when
-//                        it drops at least an eighth
-//  kgon_count_kernel     per 4096-survivor tile: exact test, keep bits,
-//                        counts (the fan in shared memory)
-//  kgon_scatter_kernel   stable compaction into the other sort buffer; sets
-//                        the survivor count and the sort's input buffer
+// The kernels run between the filter's count pass (which leaves keep bits,
+// per-tile counts and per-block totals) and its scatter pass, so the
+// scatter writes only the points that survive both tests:
+//
+//  fan_bins_kernel      octagon survivor count; per bin, the farthest sampled
+//                       input point (atomicMax of (r^2 bits << 32 | ~index),
+//                       in shared memory per block, then in global memory)
+//  fan_build_kernel     exact centre check against the octagon; the vertex
+//                       of every bin
+//  fan_estimate_kernel  exact test of an input sample: whether the fan drops
+//                       at least an eighth of the octagon's survivors
+//  fan_refine_kernel    per tile of the filter: the kept points' exact fan
+//                       test, then new keep bits, tile counts and block totals
 //
 // Test of a point p: its bin b from a binary32 pseudo-angle (a hint only),
 // v the vertex of b.  p strictly left of the ray c -> v: the triangle
@@ -42,22 +44,18 @@ namespace ch {
 namespace {
 
 constexpr int FT = 512;                  // threads per block of the bins pass
-constexpr int FITEMS = 8;                // survivors per thread per tile there
+constexpr int FITEMS = 8;                // points per thread per tile there
 constexpr int FTILE = FT * FITEMS;       // 4096
-constexpr int CT = 1024;                 // threads per block of the count and scatter passes
-constexpr int CITEMS = FTILE / CT;       // 4 survivors per thread per tile
-constexpr int CNW = CT / 32;
+constexpr int CT = 1024;                 // threads per block of the refine pass: four
+constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, one filter tile each
 constexpr int kTileSample = 4;           // the bins see every 4th tile
-constexpr uint32_t kKgonMinS = 1u << 16; // fewer survivors: not worth a pass
+constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 128 KB
-// keep words: per tile, per warp, per row r the ballot of "kept" over the
-// warp's lanes (survivor base + r * CT + warp * 32 + lane), in the filter's
-// per-tile keep-bit scratch (512 B per 4096-point tile)
-static_assert(FTILE == kFiltTile && CNW * CITEMS * 4 == kFiltThreads * 2, "keep words fit the filter's scratch");
+static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
 
-__device__ __forceinline__ float2 survivor(const uint32_t *keys, const unsigned long long *pay, int64_t q)
+__device__ __forceinline__ float2 input_point(const float *pts, int64_t i)
 {
-    return make_float2(key_float(__ldg(keys + q)), key_float((uint32_t)(__ldg(pay + q) >> 32)));
+    return __ldg(reinterpret_cast<const float2 *>(pts) + i);
 }
 
 // Bin of the direction (dx, dy): a pseudo-angle in [0, 4) that grows with
@@ -115,44 +113,56 @@ __device__ __forceinline__ bool fan_inside(const float2 *V, float cx, float cy, 
     return f != 2 ? f == 1 : fan_inside_exact(V, cx, cy, p.x, p.y);
 }
 
-__device__ __forceinline__ bool kgon_live(const Ctrl *ctrl, const Octagon *oct, uint32_t &s)
+// The fan runs when the octagon left at least kKgonMinS survivors and has
+// an edge (otherwise it does nothing).
+__device__ __forceinline__ bool fan_live(const KgonCtrl *kc, const Octagon *oct, uint32_t &s)
 {
-    s = oct->abort ? 0u : ctrl->surv_count;
+    s = oct->abort ? 0u : kc->s_oct;
     return s >= kKgonMinS && oct->has_edges;
 }
 
-__global__ void __launch_bounds__(FT) kgon_bins_kernel(void *ws, Layout L)
+// bc: the grid of the filter's count pass (its block totals are in
+// filt_bsum[0, bc)).
+__global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L,
+                                                      int32_t bc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *s_best = reinterpret_cast<unsigned long long *>(smem_raw);   // kFanBins
-    const Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    __shared__ uint32_t s_red[FT / 32];
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    uint32_t s;
-    if (!kgon_live(ctrl, oct, s)) return;
+    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
+    if (oct->abort) return;   // the count pass left no totals
+    // octagon survivors: the sum of the count pass's block totals
+    const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t t = 0;
+    for (int i = threadIdx.x; i < bc; i += FT) t += bsum[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s_red[warp] = t;
+    __syncthreads();
+    uint32_t s = 0;
+    for (int w = 0; w < FT / 32; ++w) s += s_red[w];
+    if (blockIdx.x == 0 && threadIdx.x == 0) kc->s_oct = s;
+    if (s < kKgonMinS || !oct->has_edges) return;
     for (int i = threadIdx.x; i < kFanBins; i += FT) s_best[i] = 0ull;
     __syncthreads();
     const float cx = oct->cx, cy = oct->cy;
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
-    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    const int64_t ntiles = ceil_div((int64_t)s, FTILE);
+    const int64_t ntiles = ceil_div(n, FTILE);
     const int64_t nsamp = ceil_div(ntiles, kTileSample);
     for (int64_t k = blockIdx.x; k < nsamp; k += gridDim.x) {
         const int64_t base = k * kTileSample * FTILE;
-        float x[FITEMS], y[FITEMS];
+        float2 p[FITEMS];
 #pragma unroll
         for (int r = 0; r < FITEMS; ++r) {
             const int64_t q = base + r * FT + threadIdx.x;
-            x[r] = y[r] = 0.0f;
-            if (q < s) {
-                x[r] = key_float(__ldg(keys + q));
-                y[r] = key_float(__ldg(reinterpret_cast<const uint2 *>(pay) + q).y);
-            }
+            p[r] = q < n ? input_point(pts, q) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
         for (int r = 0; r < FITEMS; ++r) {
             const int64_t q = base + r * FT + threadIdx.x;
-            if (q < s) {
-                const float dx = x[r] - cx, dy = y[r] - cy;
+            if (q < n) {
+                const float dx = p[r].x - cx, dy = p[r].y - cy;
                 const int b = fan_bin(dx, dy);
                 const float r2 = __fmaf_rn(dx, dx, dy * dy);   // >= +0
                 const unsigned long long v = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)~(uint32_t)q;
@@ -161,7 +171,6 @@ __global__ void __launch_bounds__(FT) kgon_bins_kernel(void *ws, Layout L)
         }
     }
     __syncthreads();
-    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     for (int i = threadIdx.x; i < kFanBins; i += FT) {
         const unsigned long long v = s_best[i];
         if (v != 0ull && v > __ldcg(&kc->slot[i])) atomicMax(&kc->slot[i], v);
@@ -169,22 +178,22 @@ __global__ void __launch_bounds__(FT) kgon_bins_kernel(void *ws, Layout L)
 }
 
 // One block: each thread owns PER consecutive bins.  The vertex of bin b is
-// the sampled survivor of the last non-empty bin at or before b, cyclically
+// the sampled point of the last non-empty bin at or before b, cyclically
 // (a max-scan of "last non-empty bin" over the threads).
 constexpr int BT = 1024;
 
-__global__ void __launch_bounds__(BT) kgon_build_kernel(void *ws, Layout L)
+__global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L)
 {
     constexpr int PER = kFanBins / BT;
     static_assert(kFanBins % BT == 0, "bins split evenly over the threads");
     __shared__ int s_w[BT / 32];
     __shared__ int s_ok;
-    const Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
+    const KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     Kgon *g = at<Kgon>(ws, L.kgon);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     uint32_t s;
-    if (!kgon_live(ctrl, oct, s)) {
+    if (!fan_live(kc, oct, s)) {
         if (tid == 0) g->ok = 0u;
         return;
     }
@@ -197,7 +206,6 @@ __global__ void __launch_bounds__(BT) kgon_build_kernel(void *ws, Layout L)
     if (tid < 8 && ((oct->valid >> tid) & 1u) &&
         orient(oct->ax[tid], oct->ay[tid], oct->bx[tid], oct->by[tid], cx, cy) <= 0)
         s_ok = 0;
-    const KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     unsigned long long sl[PER];
     int last = -1;
 #pragma unroll
@@ -226,15 +234,13 @@ __global__ void __launch_bounds__(BT) kgon_build_kernel(void *ws, Layout L)
     }
     int cur = max(before, ex);
     if (cur < 0) cur = all;   // before the first non-empty bin: wrap to the last one
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
-    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
     unsigned long long cv = kc->slot[cur];
     float2 pv[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {   // all loads before the stores
         if (sl[k] != 0ull) cv = sl[k];
-        const uint32_t pos = ~(uint32_t)cv;
-        pv[k] = survivor(keys, pay, pos < s ? pos : 0u);
+        const uint32_t i = ~(uint32_t)cv;
+        pv[k] = input_point(pts, (int64_t)i < n ? i : 0u);
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) g->v[tid * PER + k] = pv[k];
@@ -245,23 +251,23 @@ __global__ void __launch_bounds__(BT) kgon_build_kernel(void *ws, Layout L)
     }
 }
 
-__global__ void __launch_bounds__(256) kgon_estimate_kernel(void *ws, Layout L)
+// About 2^16 evenly spaced input points.  With f the share of them inside
+// the fan and s of n points surviving the octagon, the fan drops at least
+// f n - (n - s) of the survivors; the refine pass runs when that is at
+// least s / 8.
+__global__ void __launch_bounds__(256) fan_estimate_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L)
 {
     __shared__ uint32_t s_in[8], s_tot[8];
-    const Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     uint32_t s;
-    if (!kgon_live(ctrl, at<Octagon>(ws, L.oct), s)) return;
+    if (!fan_live(kc, at<Octagon>(ws, L.oct), s)) return;
     const Kgon *g = at<Kgon>(ws, L.kgon);
     if (!g->ok) return;
-    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
-    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    // about 2^16 evenly spaced survivors
-    const int64_t stride = std::max<int64_t>(1, (int64_t)s >> 16);
-    const int64_t nsamp = ((int64_t)s - stride / 2 + stride - 1) / stride;
+    const int64_t stride = std::max<int64_t>(1, n >> 16);
+    const int64_t nsamp = (n - stride / 2 + stride - 1) / stride;
     uint32_t in = 0, tot = 0;
     for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x; k < nsamp; k += (int64_t)gridDim.x * 256) {
-        in += fan_inside(g->v, g->cx, g->cy, survivor(keys, pay, k * stride + stride / 2)) ? 1u : 0u;
+        in += fan_inside(g->v, g->cx, g->cy, input_point(pts, k * stride + stride / 2)) ? 1u : 0u;
         ++tot;
     }
 #pragma unroll
@@ -286,222 +292,165 @@ __global__ void __launch_bounds__(256) kgon_estimate_kernel(void *ws, Layout L)
     }
 }
 
-// The pass runs when the sample says it removes at least an eighth.
-__device__ __forceinline__ bool kgon_worth(const KgonCtrl *kc) { return kc->sample > 0u && kc->inside * 8u >= kc->sample; }
+__device__ __forceinline__ bool fan_worth(const KgonCtrl *kc, int64_t n, uint32_t s)
+{
+    const double f = kc->sample ? (double)kc->inside / (double)kc->sample : 0.0;
+    return kc->sample > 0u && f * (double)n - (double)(n - s) >= (double)s / 8.0;
+}
 
-// Block b owns a contiguous range of tiles (the scatter pass uses the same
-// grid and ranges).  No barrier inside the loop: every warp writes its own
-// keep words, and the block's total is reduced once at the end.
-__global__ void __launch_bounds__(CT, 1) kgon_count_kernel(void *ws, Layout L)
+// Fan test of one half (8 items) of a filter thread's 16 kept points; the
+// item and point layout is the count pass's: item q = r * G + h is point
+// base + (r * kFiltThreads + t) * G + h.  Returns the bits (at item
+// positions) of kept points strictly inside the fan.
+template <int G>
+__device__ __forceinline__ uint32_t refine_half(const float *__restrict__ pts, int64_t n, int64_t base, uint32_t t,
+                                                uint32_t kb, int half, const float2 *sv, float cx, float cy)
+{
+    float px[8], py[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) px[k] = py[k] = 0.0f;
+    if constexpr (G == 2) {
+#pragma unroll
+        for (int r4 = 0; r4 < 4; ++r4) {
+            const int r = half * 4 + r4;
+            if ((kb >> (2 * r)) & 3u) {
+                const int64_t i = base + (int64_t)(r * kFiltThreads + t) * 2;
+                float4 v;
+                if (i + 1 < n) {
+                    v = __ldcs(reinterpret_cast<const float4 *>(pts) + i / 2);
+                } else {
+                    const float2 a = reinterpret_cast<const float2 *>(pts)[i];
+                    v = make_float4(a.x, a.y, 0.0f, 0.0f);
+                }
+                px[2 * r4] = v.x;
+                py[2 * r4] = v.y;
+                px[2 * r4 + 1] = v.z;
+                py[2 * r4 + 1] = v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = half * 8 + k;
+            if ((kb >> r) & 1u) {
+                const float2 v = __ldcs(reinterpret_cast<const float2 *>(pts) + base + r * kFiltThreads + t);
+                px[k] = v.x;
+                py[k] = v.y;
+            }
+        }
+    }
+    const uint32_t live = (kb >> (8 * half)) & 0xffu;
+    uint32_t in = 0, und = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int f = fan_signs_f32(sv, cx, cy, px[k], py[k]);
+        in |= (f == 1 ? 1u : 0u) << k;
+        und |= (f == 2 ? 1u : 0u) << k;
+    }
+    in &= live;
+    und &= live;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (((und >> k) & 1u) && fan_inside_exact(sv, cx, cy, px[k], py[k])) in |= 1u << k;
+    return in << (8 * half);
+}
+
+// Block b takes the filter's count blocks j = b, b + gridDim.x, ...; the
+// tiles of block j (its contiguous range) go four at a time to the four
+// groups of kFiltThreads threads, thread t of a group holding the 16 keep
+// bits of filter thread t.  The new tile counts and block totals replace
+// the count pass's, so the filter's scatter pass writes only the points
+// that survive both tests.
+template <int G>
+__global__ void __launch_bounds__(CT, 1) fan_refine_kernel(const float *__restrict__ pts, int64_t n, void *ws,
+                                                          Layout L, int32_t bc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sv = reinterpret_cast<float2 *>(smem_raw);   // kFanBins vertices
-    __shared__ uint32_t s_w[CNW];
-    const Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    uint32_t s;
-    if (!kgon_live(ctrl, at<Octagon>(ws, L.oct), s)) return;
+    __shared__ uint32_t s_cnt[CG];
+    const Octagon *oct = at<Octagon>(ws, L.oct);
     KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
+    uint32_t s;
+    if (!fan_live(kc, oct, s)) return;
     const Kgon *g = at<Kgon>(ws, L.kgon);
-    if (!g->ok || !kgon_worth(kc)) return;
+    if (!g->ok || !fan_worth(kc, n, s)) return;
     {
         const float4 *src = reinterpret_cast<const float4 *>(g->v);
         float4 *dst = reinterpret_cast<float4 *>(sv);
         for (int i = threadIdx.x; i < kFanBins / 2; i += CT) dst[i] = __ldg(src + i);
     }
+    if (threadIdx.x < CG) s_cnt[threadIdx.x] = 0u;
     const float cx = g->cx, cy = g->cy;
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) kc->s_in = s;
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
-    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    uint32_t *kw = at<uint32_t>(ws, L.keep_bits);
-    const int64_t ntiles = ceil_div((int64_t)s, FTILE);
-    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
-    const int64_t t1 = std::min<int64_t>(ntiles, (int64_t)(blockIdx.x + 1) * per);
-    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    uint32_t warp_total = 0;
-    for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
-        const int64_t base = tile * FTILE;
-        if (threadIdx.x == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
-            const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, (int64_t)s - base - FTILE);
-            bulk_prefetch_l2(keys + base + FTILE, (nn * 4u) & ~15u);
-            bulk_prefetch_l2(pay + base + FTILE, (nn * 8u) & ~15u);
-        }
-        float x[CITEMS], y[CITEMS];
-        const int64_t left = (int64_t)s - base - threadIdx.x;   // item r exists iff r * CT < left
-#pragma unroll
-        for (int r = 0; r < CITEMS; ++r) {
-            const int64_t q = base + r * CT + threadIdx.x;
-            x[r] = y[r] = 0.0f;
-            if ((int64_t)r * CT < left) {
-                x[r] = key_float(__ldg(keys + q));
-                y[r] = key_float(__ldg(reinterpret_cast<const uint2 *>(pay) + q).y);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
+    const int64_t ntiles = ceil_div(n, kFiltTile);
+    const int64_t per = ceil_div(ntiles, (int64_t)bc);
+    const uint32_t grp = threadIdx.x / kFiltThreads, t = threadIdx.x % kFiltThreads, lane = lane_id();
+    for (int64_t j = blockIdx.x; j < bc; j += gridDim.x) {
+        const int64_t tlo = j * per, thi = std::min<int64_t>(ntiles, tlo + per);
+        uint32_t jtotal = 0;   // thread 0
+        for (int64_t c0 = tlo; c0 < thi; c0 += CG) {
+            if (threadIdx.x == 0 && c0 + CG < thi) {   // the next tiles stream into L2 meanwhile
+                const int64_t nb = (c0 + CG) * kFiltTile;
+                const uint32_t nn = (uint32_t)std::min<int64_t>((int64_t)CG * kFiltTile, n - nb);
+                if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0)
+                    bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
             }
-        }
-        // binary32 signs for every item first, exact ones for the few
-        // undecided (both paths give the exact answer on every item they
-        // decide)
-        uint32_t keep = 0, undecided = 0, live = 0;
+            const int64_t tile = c0 + grp;
+            if (tile < thi && (uint32_t)status[tile] != 0u) {   // group-uniform
+                const int64_t base = tile * kFiltTile;
+                const uint32_t kb = bits[tile * kFiltThreads + t];
+                uint32_t in = 0;
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half)
+                    if ((kb >> (8 * half)) & 0xffu) in |= refine_half<G>(pts, n, base, t, kb, half, sv, cx, cy);
+                const uint32_t nk = kb & ~in;
+                if (nk != kb) bits[tile * kFiltThreads + t] = (uint16_t)nk;
+                uint32_t c = __popc(nk);
 #pragma unroll
-        for (int r = 0; r < CITEMS; ++r) {
-            const int f = fan_signs_f32(sv, cx, cy, x[r], y[r]);
-            keep |= (f == 0 ? 1u : 0u) << r;
-            undecided |= (f == 2 ? 1u : 0u) << r;
-            live |= ((int64_t)r * CT < left ? 1u : 0u) << r;
-        }
-        keep &= live;
-        undecided &= live;
-#pragma unroll
-        for (int r = 0; r < CITEMS; ++r)
-            if (((undecided >> r) & 1u) && !fan_inside_exact(sv, cx, cy, x[r], y[r])) keep |= 1u << r;
-        uint32_t word = 0;
-#pragma unroll
-        for (int r = 0; r < CITEMS; ++r) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (keep >> r) & 1u);
-            if (lane == (uint32_t)r) word = m;
-            warp_total += __popc(m);
-        }
-        if (lane < (uint32_t)CITEMS) kw[tile * (CNW * CITEMS) + warp * CITEMS + lane] = word;
-    }
-    if (lane == 0) s_w[warp] = warp_total;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < CNW; ++w) t += s_w[w];
-        at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = t;
-    }
-}
-
-// Same grid as the count pass (block b owns the same tile range).  Per tile:
-// each warp reads its four keep words and starts the loads of its kept
-// survivors, then one warp scans the 128 (row, warp) counts in element order.
-__global__ void __launch_bounds__(CT, 1) kgon_scatter_kernel(void *ws, Layout L)
-{
-    __shared__ uint32_t s_red[2][CNW];
-    __shared__ uint32_t s_cnt[CITEMS * CNW];   // [r][warp]
-    __shared__ uint32_t s_off[CITEMS * CNW];
-    __shared__ uint32_t s_tot;
-    __shared__ uint32_t s_flag;
-    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
-    if (threadIdx.x == 0) s_flag = kc->s_in != 0u;   // set by the count pass when it ran
-    __syncthreads();
-    if (!s_flag) return;
-    const uint32_t s = kc->s_in;
-    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
-    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
-    uint32_t *okeys = at<uint32_t>(ws, L.keys[1]);
-    unsigned long long *opay = at<unsigned long long>(ws, L.pay[1]);
-    const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
-    const uint4 *kw = at<uint4>(ws, L.keep_bits);   // one uint4 (rows 0..3) per (tile, warp)
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id(), lt = (1u << lane) - 1u;
-    uint32_t before = 0, total = 0;
-    for (uint32_t i = tid; i < gridDim.x; i += CT) {
-        const uint32_t v = bsum[i];
-        total += v;
-        if (i < blockIdx.x) before += v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        before += __shfl_xor_sync(0xffffffffu, before, o);
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-    }
-    if (lane == 0) {
-        s_red[0][warp] = before;
-        s_red[1][warp] = total;
-    }
-    __syncthreads();
-    before = total = 0;
-    for (int w = 0; w < CNW; ++w) {
-        before += s_red[0][w];
-        total += s_red[1][w];
-    }
-    if (blockIdx.x == 0 && tid == 0) {
-        ctrl->surv_count = total;
-        ctrl->sort_in = 1u;
-    }
-    const int64_t ntiles = ceil_div((int64_t)s, FTILE);
-    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
-    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = std::min<int64_t>(ntiles, r0 + per);
-    uint64_t run = before;
-    for (int64_t tile = r0; tile < r1; ++tile) {
-        const int64_t base = tile * FTILE;
-        if (tid == 0 && tile + 1 < r1) {
-            const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, (int64_t)s - base - FTILE);
-            bulk_prefetch_l2(keys + base + FTILE, (nn * 4u) & ~15u);
-            bulk_prefetch_l2(pay + base + FTILE, (nn * 8u) & ~15u);
-        }
-        const uint4 w4 = kw[tile * CNW + warp];
-        const uint32_t wd[CITEMS] = {w4.x, w4.y, w4.z, w4.w};
-        uint32_t kk[CITEMS];
-        unsigned long long kp[CITEMS];
-#pragma unroll
-        for (int r = 0; r < CITEMS; ++r) {
-            kk[r] = 0u;
-            kp[r] = 0ull;
-            if ((wd[r] >> lane) & 1u) {
-                const int64_t q = base + r * CT + tid;
-                kk[r] = __ldg(keys + q);
-                kp[r] = __ldg(pay + q);
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (lane == 0) atomicAdd(&s_cnt[grp], c);
             }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < CG; ++k) {
+                    if (c0 + k < thi) {
+                        status[c0 + k] = s_cnt[k];
+                        jtotal += s_cnt[k];
+                    }
+                    s_cnt[k] = 0u;
+                }
+            }
+            __syncthreads();
         }
-        if (lane < (uint32_t)CITEMS) s_cnt[lane * CNW + warp] = __popc(wd[lane]);
-        __syncthreads();
-        if (warp == 0) {   // exclusive scan of the counts in (row, warp) order
-            constexpr int PER = CITEMS * CNW / 32;
-            uint32_t loc[PER], sum = 0;
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                loc[k] = s_cnt[lane * PER + k];
-                sum += loc[k];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (uint32_t)o) incl += t;
-            }
-            uint32_t ex = incl - sum;
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                s_off[lane * PER + k] = ex;
-                ex += loc[k];
-            }
-            if (lane == 31) s_tot = incl;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < CITEMS; ++r) {
-            if ((wd[r] >> lane) & 1u) {
-                const uint64_t pos = run + s_off[r * CNW + warp] + __popc(wd[r] & lt);
-                okeys[pos] = kk[r];
-                opay[pos] = kp[r];
-            }
-        }
-        run += s_tot;
+        if (threadIdx.x == 0) bsum[j] = jtotal;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_kgon(void *ws, const Layout &L, cudaStream_t st)
+cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blocks, void *ws, const Layout &L,
+                       cudaStream_t st)
 {
     const int sms = sm_count();
-    static int per_sm = [] {
-        cudaFuncSetAttribute(kgon_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
-        cudaFuncSetAttribute(kgon_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
-        int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kgon_count_kernel, CT, kFanSmem);
-        return v > 0 ? v : 1;
+    static const bool attrs = [] {
+        cudaFuncSetAttribute(fan_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
+        cudaFuncSetAttribute(fan_refine_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
+        cudaFuncSetAttribute(fan_refine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
+        return true;
     }();
-    const int64_t tiles = ceil_div(L.n, FTILE);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>({tiles, (int64_t)sms * per_sm, kFiltMaxBlocks}));
+    (void)attrs;
+    const int32_t bc = (int32_t)filter_blocks;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, filter_blocks));
     probe_before(CH_K_KGON, st);
-    kgon_bins_kernel<<<sms, FT, kFanSmem, st>>>(ws, L);
-    kgon_build_kernel<<<1, BT, 0, st>>>(ws, L);
-    kgon_estimate_kernel<<<sms, 256, 0, st>>>(ws, L);
-    kgon_count_kernel<<<(unsigned)grid, CT, kFanSmem, st>>>(ws, L);
-    kgon_scatter_kernel<<<(unsigned)grid, CT, 0, st>>>(ws, L);
-    note_kernels(CH_K_KGON, 5);
+    fan_bins_kernel<<<sms, FT, kFanSmem, st>>>(pts, n, ws, L, bc);
+    fan_build_kernel<<<1, BT, 0, st>>>(pts, n, ws, L);
+    fan_estimate_kernel<<<sms, 256, 0, st>>>(pts, n, ws, L);
+    if (vec) fan_refine_kernel<2><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
+    else fan_refine_kernel<1><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
+    note_kernels(CH_K_KGON, 4);
     probe_after(CH_K_KGON, st);
     return cudaGetLastError();
 }

@@ -27,13 +27,17 @@ cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, vo
 // point test + stable compaction.  keys_mode: write (x key, (y key, index))
 // pairs into the sort buffers of ws instead of (index, point) outputs.
 // variant: 0 two passes (needs keep_bits in L), 1 single pass, -1 the
-// process-wide choice of ch_filter_variant.
+// process-wide choice of ch_filter_variant.  fan (hull step, two passes
+// only): launch_fan between the count and the scatter pass.
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
-                          int variant = -1);
+                          int variant = -1, bool fan = false);
 
-// second throw-away polygon over the survivors (hull step; may do nothing)
-cudaError_t launch_kgon(void *ws, const Layout &L, cudaStream_t st);
+// hull step: the fan test applied to the keep bits, tile counts and block
+// totals that the filter's count pass (filter_blocks blocks) left in ws;
+// may do nothing.  vec: the count pass used 16-byte point pairs.
+cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blocks, void *ws, const Layout &L,
+                       cudaStream_t st);
 
 // stable LSD radix sort of the survivor (key, index) pairs held in ws
 cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);
