@@ -79,7 +79,9 @@ struct ExtCtrl {
 
 // second throw-away step of the hull step (kgon.cu): a fan of triangles
 // around the bounding-box centre, one vertex per angular bin
-constexpr int kFanBins = 16384;
+// (28672 vertices of 8 bytes fill 224 KB: as many as one block's shared
+// memory holds)
+constexpr int kFanBins = 28672;
 
 struct KgonCtrl {                          // zeroed with the control block
     unsigned long long slot[kFanBins];     // packed (r^2 bits << 32 | ~index): farthest sampled input point per bin

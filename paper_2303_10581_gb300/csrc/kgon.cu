@@ -50,7 +50,7 @@ constexpr int CT = 1024;                 // threads per block of the refine pass
 constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, one filter tile each
 constexpr int kTileSample = 4;           // the bins see every 4th tile
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
-constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 128 KB
+constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
 static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
 
 __device__ __forceinline__ float2 input_point(const float *pts, int64_t i)
@@ -74,6 +74,9 @@ __device__ __forceinline__ int fan_bin(float dx, float dy)
     return b < 0 ? 0 : (b >= kFanBins ? kFanBins - 1 : b);
 }
 
+__device__ __forceinline__ int next_bin(int b) { return b + 1 == kFanBins ? 0 : b + 1; }
+__device__ __forceinline__ int prev_bin(int b) { return b == 0 ? kFanBins - 1 : b - 1; }
+
 // Strictly inside a fan triangle (exact signs).  V: kFanBins vertices.
 // With o = orient(c, v, p) = +1 the triangle is (c, v, w), w the next
 // vertex, and p is inside iff orient(v, w, p) = orient(w, c, p) = +1; with
@@ -90,7 +93,7 @@ __device__ __forceinline__ int fan_signs_f32(const float2 *V, float cx, float cy
     const int b = fan_bin(px - cx, py - cy);
     const float2 v = V[b];
     const int o = orient_f32(cx, cy, v.x, v.y, px, py);
-    const float2 w = V[(b + (o == 1 ? 1 : -1)) & (kFanBins - 1)];
+    const float2 w = V[o == 1 ? next_bin(b) : prev_bin(b)];
     const int e1 = orient_f32(v.x, v.y, w.x, w.y, px, py);
     const int e2 = orient_f32(w.x, w.y, cx, cy, px, py);
     const bool out = (e1 != 2 && e1 != o) || (e2 != 2 && e2 != o);
@@ -103,7 +106,7 @@ __device__ __noinline__ bool fan_inside_exact(const float2 *V, float cx, float c
     const float2 v = V[b];
     const int o = orient(cx, cy, v.x, v.y, px, py);
     if (o == 0) return false;
-    const float2 w = V[(b + o) & (kFanBins - 1)];
+    const float2 w = V[o > 0 ? next_bin(b) : prev_bin(b)];
     return orient(v.x, v.y, w.x, w.y, px, py) == o && orient(w.x, w.y, cx, cy, px, py) == o;
 }
 
@@ -206,13 +209,10 @@ __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__
     if (tid < 8 && ((oct->valid >> tid) & 1u) &&
         orient(oct->ax[tid], oct->ay[tid], oct->bx[tid], oct->by[tid], cx, cy) <= 0)
         s_ok = 0;
-    unsigned long long sl[PER];
+    const unsigned long long *slot = kc->slot + (size_t)tid * PER;
     int last = -1;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        sl[k] = kc->slot[tid * PER + k];
-        if (sl[k] != 0ull) last = (int)(tid * PER + k);
-    }
+    for (int k = 0; k < PER; ++k)
+        if (slot[k] != 0ull) last = (int)(tid * PER + k);
     int incl = last;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -235,15 +235,20 @@ __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__
     int cur = max(before, ex);
     if (cur < 0) cur = all;   // before the first non-empty bin: wrap to the last one
     unsigned long long cv = kc->slot[cur];
-    float2 pv[PER];
+    constexpr int CH = 4;   // vertices loaded before they are stored
+    static_assert(PER % CH == 0, "whole chunks");
+    for (int k0 = 0; k0 < PER; k0 += CH) {
+        float2 pv[CH];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {   // all loads before the stores
-        if (sl[k] != 0ull) cv = sl[k];
-        const uint32_t i = ~(uint32_t)cv;
-        pv[k] = input_point(pts, (int64_t)i < n ? i : 0u);
+        for (int k = 0; k < CH; ++k) {
+            const unsigned long long v = slot[k0 + k];
+            if (v != 0ull) cv = v;
+            const uint32_t i = ~(uint32_t)cv;
+            pv[k] = input_point(pts, (int64_t)i < n ? i : 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) g->v[tid * PER + k0 + k] = pv[k];
     }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) g->v[tid * PER + k] = pv[k];
     if (tid == 0) {
         g->cx = cx;
         g->cy = cy;
