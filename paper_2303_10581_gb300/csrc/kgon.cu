@@ -47,7 +47,7 @@ constexpr int FT = 512;                  // threads per block of the bins pass
 constexpr int FITEMS = 8;                // points per thread per tile there
 constexpr int FTILE = FT * FITEMS;       // 4096
 constexpr int CT = 1024;                 // threads per block of the refine pass: four
-constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, one filter tile each
+constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, each with its own tiles
 constexpr int kTileSample = 4;           // the bins see every 4th tile
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
@@ -180,16 +180,30 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     }
 }
 
-// One block: each thread owns PER consecutive bins.  The vertex of bin b is
-// the sampled point of the last non-empty bin at or before b, cyclically
-// (a max-scan of "last non-empty bin" over the threads).
+// One thread per bin (kFanBins / BT blocks).  The vertex of bin b is the
+// sampled point of the last non-empty bin at or before b, cyclically: a
+// max-scan of "non-empty bin index" inside the block, and for the bins
+// before the block's first non-empty one, the last non-empty bin of the
+// nearest earlier range of BT bins that has one (searched range by range).
 constexpr int BT = 1024;
+static_assert(kFanBins % BT == 0, "bins split evenly over the blocks");
+
+__device__ __forceinline__ int block_max(int v, int *s_w)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();   // s_w may still be read from an earlier call
+    if (lane_id() == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int m = -1;
+    for (int w = 0; w < BT / 32; ++w) m = max(m, s_w[w]);
+    return m;
+}
 
 __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L)
 {
-    constexpr int PER = kFanBins / BT;
-    static_assert(kFanBins % BT == 0, "bins split evenly over the threads");
     __shared__ int s_w[BT / 32];
+    __shared__ int s_scan[BT / 32];
     __shared__ int s_ok;
     const Octagon *oct = at<Octagon>(ws, L.oct);
     const KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
@@ -197,7 +211,7 @@ __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     uint32_t s;
     if (!fan_live(kc, oct, s)) {
-        if (tid == 0) g->ok = 0u;
+        if (blockIdx.x == 0 && tid == 0) g->ok = 0u;
         return;
     }
     const float cx = oct->cx, cy = oct->cy;
@@ -209,47 +223,33 @@ __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__
     if (tid < 8 && ((oct->valid >> tid) & 1u) &&
         orient(oct->ax[tid], oct->ay[tid], oct->bx[tid], oct->by[tid], cx, cy) <= 0)
         s_ok = 0;
-    const unsigned long long *slot = kc->slot + (size_t)tid * PER;
-    int last = -1;
-    for (int k = 0; k < PER; ++k)
-        if (slot[k] != 0ull) last = (int)(tid * PER + k);
-    int incl = last;
+    const int b = (int)(blockIdx.x * BT + tid);
+    const unsigned long long mine = kc->slot[b];
+    int incl = mine != 0ull ? b : -1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int u = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= (uint32_t)o) incl = max(incl, u);
     }
-    int ex = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) ex = -1;
-    if (lane == 31) s_w[warp] = incl;
+    if (lane == 31) s_scan[warp] = incl;
     __syncthreads();
-    int before = -1, all = -1;
-    for (int w = 0; w < BT / 32; ++w) {
-        if (w < (int)warp) before = max(before, s_w[w]);
-        all = max(all, s_w[w]);
+    for (int w = 0; w < (int)warp; ++w) incl = max(incl, s_scan[w]);
+    // the nearest earlier range with a non-empty bin (the block's own range
+    // last, for the wrap-around)
+    int prev = -1;
+    for (uint32_t k = 1; k <= gridDim.x && prev < 0; ++k) {   // prev is block-uniform
+        const uint32_t rb = (blockIdx.x + gridDim.x - k) % gridDim.x;
+        const int j = (int)(rb * BT + tid);
+        prev = block_max(kc->slot[j] != 0ull ? j : -1, s_w);
     }
-    if (all < 0 || !s_ok) {   // block-uniform
-        if (tid == 0) g->ok = 0u;
+    if (prev < 0 || !s_ok) {   // no sampled point at all, or c not inside
+        if (blockIdx.x == 0 && tid == 0) g->ok = 0u;
         return;
     }
-    int cur = max(before, ex);
-    if (cur < 0) cur = all;   // before the first non-empty bin: wrap to the last one
-    unsigned long long cv = kc->slot[cur];
-    constexpr int CH = 4;   // vertices loaded before they are stored
-    static_assert(PER % CH == 0, "whole chunks");
-    for (int k0 = 0; k0 < PER; k0 += CH) {
-        float2 pv[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const unsigned long long v = slot[k0 + k];
-            if (v != 0ull) cv = v;
-            const uint32_t i = ~(uint32_t)cv;
-            pv[k] = input_point(pts, (int64_t)i < n ? i : 0u);
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) g->v[tid * PER + k0 + k] = pv[k];
-    }
-    if (tid == 0) {
+    const int cur = incl >= 0 ? incl : prev;
+    const uint32_t i = ~(uint32_t)(cur == b ? mine : kc->slot[cur]);
+    g->v[b] = input_point(pts, (int64_t)i < n ? i : 0u);
+    if (blockIdx.x == 0 && tid == 0) {
         g->cx = cx;
         g->cy = cy;
         g->ok = 1u;
@@ -303,10 +303,18 @@ __device__ __forceinline__ bool fan_worth(const KgonCtrl *kc, int64_t n, uint32_
     return kc->sample > 0u && f * (double)n - (double)(n - s) >= (double)s / 8.0;
 }
 
-// Fan test of one half (8 items) of a filter thread's 16 kept points; the
-// item and point layout is the count pass's: item q = r * G + h is point
-// base + (r * kFiltThreads + t) * G + h.  Returns the bits (at item
-// positions) of kept points strictly inside the fan.
+// Point of item q (of this thread's 16) of a filter tile; the layout is the
+// count pass's: item q = r * G + h is point base + (r * kFiltThreads + t) * G + h.
+template <int G>
+__device__ __forceinline__ int64_t item_point(int64_t base, uint32_t t, int q)
+{
+    return base + (int64_t)((q / G) * kFiltThreads + t) * G + q % G;
+}
+
+// Fan test of one half (items 8 half .. 8 half + 7) of a filter thread's
+// kept points.  Returns the bits (at item positions) of kept points strictly
+// inside the fan.  The coordinates of the few undecided points are read
+// again for the exact test, so none stay live across it.
 template <int G>
 __device__ __forceinline__ uint32_t refine_half(const float *__restrict__ pts, int64_t n, int64_t base, uint32_t t,
                                                 uint32_t kb, int half, const float2 *sv, float cx, float cy)
@@ -354,25 +362,27 @@ __device__ __forceinline__ uint32_t refine_half(const float *__restrict__ pts, i
     }
     in &= live;
     und &= live;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (((und >> k) & 1u) && fan_inside_exact(sv, cx, cy, px[k], py[k])) in |= 1u << k;
+    while (und) {
+        const int k = __ffs(und) - 1;
+        und &= und - 1u;
+        const float2 p = reinterpret_cast<const float2 *>(pts)[item_point<G>(base, t, 8 * half + k)];
+        if (fan_inside_exact(sv, cx, cy, p.x, p.y)) in |= 1u << k;
+    }
     return in << (8 * half);
 }
 
-// Block b takes the filter's count blocks j = b, b + gridDim.x, ...; the
-// tiles of block j (its contiguous range) go four at a time to the four
-// groups of kFiltThreads threads, thread t of a group holding the 16 keep
-// bits of filter thread t.  The new tile counts and block totals replace
-// the count pass's, so the filter's scatter pass writes only the points
-// that survive both tests.
+// The tiles of the filter go in contiguous ranges to groups of
+// kFiltThreads threads (four per block); thread t of a group holds the 16
+// keep bits of filter thread t.  Kept points strictly inside the fan lose
+// their keep bit, and the tile's count and its count block's total drop by
+// the number removed (atomics: no barrier in the loop), so the filter's
+// scatter pass writes only the points that survive both tests.
 template <int G>
 __global__ void __launch_bounds__(CT, 1) fan_refine_kernel(const float *__restrict__ pts, int64_t n, void *ws,
                                                           Layout L, int32_t bc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sv = reinterpret_cast<float2 *>(smem_raw);   // kFanBins vertices
-    __shared__ uint32_t s_cnt[CG];
     const Octagon *oct = at<Octagon>(ws, L.oct);
     KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     uint32_t s;
@@ -384,53 +394,37 @@ __global__ void __launch_bounds__(CT, 1) fan_refine_kernel(const float *__restri
         float4 *dst = reinterpret_cast<float4 *>(sv);
         for (int i = threadIdx.x; i < kFanBins / 2; i += CT) dst[i] = __ldg(src + i);
     }
-    if (threadIdx.x < CG) s_cnt[threadIdx.x] = 0u;
     const float cx = g->cx, cy = g->cy;
     __syncthreads();
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    const int64_t per = ceil_div(ntiles, (int64_t)bc);
+    const int64_t per_block = ceil_div(ntiles, (int64_t)bc);   // tiles per count block
     const uint32_t grp = threadIdx.x / kFiltThreads, t = threadIdx.x % kFiltThreads, lane = lane_id();
-    for (int64_t j = blockIdx.x; j < bc; j += gridDim.x) {
-        const int64_t tlo = j * per, thi = std::min<int64_t>(ntiles, tlo + per);
-        uint32_t jtotal = 0;   // thread 0
-        for (int64_t c0 = tlo; c0 < thi; c0 += CG) {
-            if (threadIdx.x == 0 && c0 + CG < thi) {   // the next tiles stream into L2 meanwhile
-                const int64_t nb = (c0 + CG) * kFiltTile;
-                const uint32_t nn = (uint32_t)std::min<int64_t>((int64_t)CG * kFiltTile, n - nb);
-                if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0)
-                    bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
-            }
-            const int64_t tile = c0 + grp;
-            if (tile < thi && (uint32_t)status[tile] != 0u) {   // group-uniform
-                const int64_t base = tile * kFiltTile;
-                const uint32_t kb = bits[tile * kFiltThreads + t];
-                uint32_t in = 0;
-#pragma unroll 1
-                for (int half = 0; half < 2; ++half)
-                    if ((kb >> (8 * half)) & 0xffu) in |= refine_half<G>(pts, n, base, t, kb, half, sv, cx, cy);
-                const uint32_t nk = kb & ~in;
-                if (nk != kb) bits[tile * kFiltThreads + t] = (uint16_t)nk;
-                uint32_t c = __popc(nk);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                if (lane == 0) atomicAdd(&s_cnt[grp], c);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int k = 0; k < CG; ++k) {
-                    if (c0 + k < thi) {
-                        status[c0 + k] = s_cnt[k];
-                        jtotal += s_cnt[k];
-                    }
-                    s_cnt[k] = 0u;
-                }
-            }
-            __syncthreads();
+    const int64_t groups = (int64_t)gridDim.x * CG, gi = (int64_t)blockIdx.x * CG + grp;
+    const int64_t per = ceil_div(ntiles, groups);
+    const int64_t t1 = std::min<int64_t>(ntiles, (gi + 1) * per);
+    for (int64_t tile = gi * per; tile < t1; ++tile) {
+        const int64_t base = tile * kFiltTile;
+        if (t == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const uint32_t nn = (uint32_t)std::min<int64_t>(kFiltTile, n - base - kFiltTile);
+            if (((reinterpret_cast<uintptr_t>(pts + 2 * (base + kFiltTile))) & 15u) == 0)
+                bulk_prefetch_l2(pts + 2 * (base + kFiltTile), (nn * 8u) & ~15u);
         }
-        if (threadIdx.x == 0) bsum[j] = jtotal;
+        const uint32_t kb = bits[tile * kFiltThreads + t];
+        uint32_t in = 0;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half)
+            if ((kb >> (8 * half)) & 0xffu) in |= refine_half<G>(pts, n, base, t, kb, half, sv, cx, cy);
+        if (in) bits[tile * kFiltThreads + t] = (uint16_t)(kb & ~in);
+        uint32_t removed = __popc(in);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) removed += __shfl_xor_sync(0xffffffffu, removed, o);
+        if (lane == 0 && removed) {
+            atomicAdd(&status[tile], 0ull - (unsigned long long)removed);   // count - removed >= 0
+            atomicSub(&bsum[tile / per_block], removed);
+        }
     }
 }
 
@@ -451,7 +445,7 @@ cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blo
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, filter_blocks));
     probe_before(CH_K_KGON, st);
     fan_bins_kernel<<<sms, FT, kFanSmem, st>>>(pts, n, ws, L, bc);
-    fan_build_kernel<<<1, BT, 0, st>>>(pts, n, ws, L);
+    fan_build_kernel<<<kFanBins / BT, BT, 0, st>>>(pts, n, ws, L);
     fan_estimate_kernel<<<sms, 256, 0, st>>>(pts, n, ws, L);
     if (vec) fan_refine_kernel<2><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
     else fan_refine_kernel<1><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
