@@ -812,10 +812,12 @@ __global__ void __launch_bounds__(32) bx_merge_kernel(void *ws, Layout L, BatchL
 }
 
 // Compacts the live chain ranges of super-chunks [0, nc): thread =
-// super-chunk, look-back over tiles of super-chunks, warp-cooperative
-// copies of the original indices (low half of the payload).  Side 0 goes to
-// out0, side 1 to out1.  With sc_off, each super-chunk's output offset per
-// side is recorded too (sc_off[side][nc] = side total).
+// super-chunk, look-back over tiles of super-chunks, then the whole block
+// copies the tile's ranges (the original indices: low half of the payload),
+// each thread finding the super-chunk of an output position by binary
+// search over the tile's offsets.  Side 0 goes to out0, side 1 to out1.
+// With sc_off, each super-chunk's output offset per side is recorded too
+// (sc_off[side][nc] = side total).
 struct EmitArgs {
     uint32_t *out[2];
     uint32_t *sc_off[2];
@@ -832,6 +834,9 @@ __device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_wsum[2][NW];
     __shared__ unsigned long long s_excl[2];
+    __shared__ uint32_t s_rel[2][kEmitThreads];   // offset of each super-chunk's range in the tile's output
+    __shared__ int32_t s_lo[2][kEmitThreads];     // and its first chain slot
+    __shared__ uint32_t s_tot[2];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(E.ticket, 1u);
@@ -882,6 +887,7 @@ __device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t
             }
             if (lane == 0) {
                 s_excl[side] = excl;
+                s_tot[side] = total;
                 if (tile == ntiles - 1) {
                     *E.h_total[side] = (uint32_t)(excl + total);
                     if (E.sc_off[side]) E.sc_off[side][nc] = (uint32_t)(excl + total);
@@ -891,19 +897,42 @@ __device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t
         __syncthreads();
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const uint64_t mypos = s_excl[side] + s_wsum[side][warp] + pre[side];
-            if (E.sc_off[side] && c < nc) E.sc_off[side][c] = (uint32_t)mypos;
+            const uint32_t rel = s_wsum[side][warp] + pre[side];
+            s_rel[side][tid] = rel;
+            s_lo[side][tid] = lo[side];
+            if (E.sc_off[side] && c < nc) E.sc_off[side][c] = (uint32_t)(s_excl[side] + rel);
+        }
+        __syncthreads();
+        constexpr int B4 = 4;   // output positions per thread in flight
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const uint32_t T = s_tot[side];
+            const uint64_t excl = s_excl[side];
             uint32_t *out = E.out[side];
             const uint32_t *chain = P.pos[side];
-            for (int i = 0; i < 32; ++i) {
-                const int32_t n_i = __shfl_sync(0xffffffffu, cnt[side], i);
-                if (n_i == 0) continue;
-                const int32_t lo_i = __shfl_sync(0xffffffffu, lo[side], i);
-                const uint64_t pos_i = __shfl_sync(0xffffffffu, mypos, i);
-                const int64_t ci = tile * kEmitThreads + warp * 32 + i;
-                for (int32_t k = (int32_t)lane; k < n_i; k += 32) {
-                    const uint32_t sp = __ldcg(chain + ci * CS + lo_i + k);
-                    if (pos_i + k < (uint64_t)s) out[pos_i + k] = (uint32_t)__ldg(P.pay + sp);
+            for (uint32_t k0 = 0; k0 < T; k0 += B4 * kEmitThreads) {
+                uint32_t sp[B4];
+#pragma unroll
+                for (int u = 0; u < B4; ++u) {
+                    const uint32_t k = k0 + u * kEmitThreads + tid;
+                    sp[u] = 0u;
+                    if (k < T) {
+                        // the last super-chunk whose range starts at or before k
+                        // (empty ranges share their start with the next one)
+                        int lo_j = 0, hi_j = kEmitThreads - 1;
+                        while (lo_j < hi_j) {
+                            const int mid = (lo_j + hi_j + 1) >> 1;
+                            if (s_rel[side][mid] <= k) lo_j = mid;
+                            else hi_j = mid - 1;
+                        }
+                        const int64_t ci = tile * kEmitThreads + lo_j;
+                        sp[u] = __ldcg(chain + ci * CS + s_lo[side][lo_j] + (k - s_rel[side][lo_j]));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < B4; ++u) {
+                    const uint32_t k = k0 + u * kEmitThreads + tid;
+                    if (k < T && excl + k < (uint64_t)s) out[excl + k] = (uint32_t)__ldg(P.pay + sp[u]);
                 }
             }
         }
