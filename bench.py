@@ -190,6 +190,33 @@ def load_traffic(kernel):
         return None
 
 
+def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev):
+    """Roofline of the fan kernels, which are bound by instruction issue,
+    not by HBM: warp instructions issued per second against the SMs' issue
+    rate (4 warp schedulers per SM, one warp instruction each per clock, at
+    the highest SM clock seen).  The instructions per octagon survivor come
+    from an ncu capture (profiles/traffic.json, void once kgon.cu changed);
+    the time is the event time of the timed launches."""
+    import torch
+
+    tr = load_traffic("kgon")
+    if not tr or "warp_inst_per_survivor" not in tr:
+        return None
+    fan_s = sum(s for s, t in zip(s_list, t_list) if t < s)   # sets whose fan pass ran
+    inst = tr["warp_inst_per_survivor"] * fan_s * steps
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * mhz * 1e6 / 1e12                          # T warp-instructions/s
+    achieved = inst / (dom_ms * 1e-3) / 1e12
+    per_launch_bytes = algorithmic_bytes("kgon", n, s_list, t_list) * steps / dom_launches
+    return {"kernel": "kgon", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T warp-instr/s", "frac": round(achieved / peak, 4),
+            "peak_source": f"derived: {sms} SMs x 4 issue slots x {mhz:.0f} MHz",
+            "traffic": int(tr["dram_per_algorithmic_byte"] * per_launch_bytes),
+            "traffic_source": tr["capture"], "algorithmic_bytes_per_launch": int(per_launch_bytes),
+            "warp_instr_per_launch": int(inst / dom_launches), "avg_launch_ms": round(dom_ms / dom_launches, 4)}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -318,7 +345,9 @@ def run_ours(args):
     dom_ms, dom_launches = probe[dominant]
     peak, peak_kind = peaks()
     roof = None
-    if dom_launches:
+    if dom_launches and dominant == "kgon":
+        roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev)
+    if dom_launches and roof is None:
         per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts)
         if per_step_bytes is not None:
             # algorithmic bytes of all timed launches over their summed event
