@@ -17,6 +17,7 @@ namespace ch {
 // launch geometry
 // ---------------------------------------------------------------------------
 constexpr int kExtThreads = 512;      // extremes sweep
+constexpr int kExtPairs = 2048;       // point pairs (16 B) per extremes tile: 32 KB
 constexpr int kFiltThreads = 256;     // fused test + compaction
 constexpr int kFiltItems = 16;        // points per thread per tile
 constexpr int kFiltTile = kFiltThreads * kFiltItems;   // 4096 points = 32 KB

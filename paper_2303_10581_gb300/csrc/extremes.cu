@@ -176,31 +176,37 @@ __global__ void __launch_bounds__(kExtThreads) extremes_kernel(const float *__re
     const int64_t head = (addr & 15u) ? 1 : 0;  // points before the 16-byte boundary
     const int64_t npairs = (n - head) / 2;
     const float4 *p4 = reinterpret_cast<const float4 *>(pts + 2 * head);
-    int64_t q = gtid;
-    for (; q + 3 * gthreads < npairs; q += 4 * gthreads) {
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldcs(p4 + q + u * gthreads);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t i0 = (uint32_t)(head + 2 * (q + u * gthreads));
-            nf = __fmaf_rn(v[u].x, 0.0f, nf);
-            nf = __fmaf_rn(v[u].y, 0.0f, nf);
-            nf = __fmaf_rn(v[u].z, 0.0f, nf);
-            nf = __fmaf_rn(v[u].w, 0.0f, nf);
-            consider(b, v[u].x, v[u].y, i0);
-            consider(b, v[u].z, v[u].w, i0 + 1);
+    // each block a contiguous range of tiles of kExtPairs point pairs; the
+    // next tile streams into L2 while this one is reduced
+    constexpr int U = kExtPairs / kExtThreads;
+    const int64_t ntiles = ceil_div(npairs, (int64_t)kExtPairs);
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
+    for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
+        const int64_t q0 = tile * kExtPairs;
+        if (threadIdx.x == 0 && tile + 1 < t1) {
+            const int64_t nq = min((int64_t)kExtPairs, npairs - q0 - kExtPairs);
+            bulk_prefetch_l2(p4 + q0 + kExtPairs, (uint32_t)(nq * 16));
         }
-    }
-    for (; q < npairs; q += gthreads) {
-        const float4 v = __ldcs(p4 + q);
-        const uint32_t i0 = (uint32_t)(head + 2 * q);
-        nf = __fmaf_rn(v.x, 0.0f, nf);
-        nf = __fmaf_rn(v.y, 0.0f, nf);
-        nf = __fmaf_rn(v.z, 0.0f, nf);
-        nf = __fmaf_rn(v.w, 0.0f, nf);
-        consider(b, v.x, v.y, i0);
-        consider(b, v.z, v.w, i0 + 1);
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t q = q0 + u * kExtThreads + threadIdx.x;
+            v[u] = q < npairs ? __ldcs(p4 + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t q = q0 + u * kExtThreads + threadIdx.x;
+            if (q < npairs) {
+                const uint32_t i0 = (uint32_t)(head + 2 * q);
+                nf = __fmaf_rn(v[u].x, 0.0f, nf);
+                nf = __fmaf_rn(v[u].y, 0.0f, nf);
+                nf = __fmaf_rn(v[u].z, 0.0f, nf);
+                nf = __fmaf_rn(v[u].w, 0.0f, nf);
+                consider(b, v[u].x, v[u].y, i0);
+                consider(b, v[u].z, v[u].w, i0 + 1);
+            }
+        }
     }
     // the point before the aligned body and the odd point after it
     if (gtid == 0 && head) {
@@ -437,9 +443,14 @@ cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout 
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
                             cudaStream_t st)
 {
+    static int per_sm = [] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, extremes_kernel, kExtThreads, 0);
+        return v > 0 ? v : 1;
+    }();
     const int64_t pairs = (n + 1) / 2;
-    int64_t blocks = ceil_div(pairs, (int64_t)kExtThreads * 4);
-    const int64_t cap = (int64_t)sm_count() * 4;
+    int64_t blocks = ceil_div(pairs, (int64_t)kExtPairs);   // one wave: every block resident
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     probe_before(CH_K_EXTREMES, st);

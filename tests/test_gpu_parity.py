@@ -229,14 +229,47 @@ def _kgon_case(case, rng):
         return (pointgen.make_points("displaced", 200_000, seed=44) * np.float32(1e-30)).astype(np.float32)
     if case == "huge_scale":
         return (pointgen.make_points("displaced", 200_000, seed=45) * np.float32(1e30)).astype(np.float32)
+    if case == "four_wedges":   # most fan bins see no sample point
+        th = rng.uniform(-0.05, 0.05, 300_000) + rng.integers(0, 4, 300_000) * (np.pi / 2)
+        r = 1.0 - np.abs(rng.standard_normal(300_000)) * 0.01
+        return np.stack([r * np.cos(th), r * np.sin(th)], 1).astype(np.float32)
+    if case == "half_ring":
+        th = rng.uniform(0.0, np.pi, 300_000)
+        return np.stack([np.cos(th), np.sin(th)], 1).astype(np.float32)
     raise ValueError(case)
 
 
 @pytest.mark.parametrize("case", ["displaced_ellipse", "ring_outliers", "collinear_big", "duplicated_ring",
-                                  "square_boundary", "tiny_scale", "huge_scale"])
+                                  "square_boundary", "tiny_scale", "huge_scale", "four_wedges", "half_ring"])
 def test_second_polygon_cases(case):
-    """Inputs with at least 2^16 survivors, so the hull step's second polygon
-    (sample extremes along many directions) is built and, where it removes
-    enough, applied -- including degenerate polygons and extreme scales."""
+    """Inputs with at least 2^16 octagon survivors, so the hull step's fan
+    (vertices: the farthest sampled points of angular bins around the
+    bounding-box centre) is built and, where it removes enough, applied --
+    including fans with flat or clockwise triangles, bins without samples,
+    points on fan edges and extreme scales."""
     p = _kgon_case(case, np.random.default_rng(7))
     check_against_oracle(p)
+
+
+@pytest.mark.parametrize("dist", ["circle", "displaced"])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_fan_removes_points_and_keeps_the_hull(dist, aligned):
+    """On circle-like sets the fan drops octagon survivors before the sort
+    (fewer points sorted than survived the octagon), for 16-byte-aligned
+    point pairs and for an 8-byte-aligned view (the two refine kernels), and
+    the hull is still the oracle's."""
+    p = pointgen.make_points(dist, 1_000_003, seed=91)
+    if aligned:
+        d = dev(p)
+    else:
+        d = dev(np.concatenate([np.zeros((1, 2), np.float32), p]))[1:]
+        assert d.data_ptr() % 16 == 8
+    ws = ch.Workspace(len(p))
+    hidx, hcnt = ch.convex_hull(d, ws)
+    torch.cuda.synchronize()
+    assert ch.ch_last_error(ws.buf) == ch.CH_OK
+    s_oct, t = ch.ch_hull_counts(ws.buf, len(p))
+    _, os_, oh = oracle.convex_hull(p)
+    assert s_oct == len(os_)
+    assert t < (s_oct if dist == "circle" else s_oct // 4), (s_oct, t)
+    assert np.array_equal(hidx[: int(hcnt.item())].cpu().numpy().view(np.uint32), oh)
