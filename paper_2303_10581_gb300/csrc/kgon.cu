@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     const int64_t nsamp = ceil_div(ntiles, kTileSample);
     for (int64_t k = blockIdx.x; k < nsamp; k += gridDim.x) {
         const int64_t base = k * kTileSample * FTILE;
+        if (threadIdx.x == 0 && k + gridDim.x < nsamp) {   // this block's next sample tile streams into L2
+            const int64_t nb = (k + gridDim.x) * kTileSample * FTILE;
+            const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, n - nb);
+            if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
+        }
         float2 p[FITEMS];
 #pragma unroll
         for (int r = 0; r < FITEMS; ++r) {
