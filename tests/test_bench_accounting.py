@@ -1,0 +1,54 @@
+"""The bench's roofline bookkeeping on CPU: algorithmic bytes per kernel
+follow their definitions, the fan group's ALU roofline uses the recorded
+instructions per survivor only while kgon.cu is unchanged, and counts only
+the sets whose fan ran."""
+import copy
+import json
+
+import pytest
+import torch
+
+import bench
+
+N = 10**8
+S = [69, 99_999_997, 94_825_784]     # octagon survivors
+T = [69, 16_543_492, 118_191]        # points sorted after the fan
+
+
+def test_algorithmic_bytes_definitions():
+    assert bench.algorithmic_bytes("extremes", N, S, T) == 3 * 8 * N
+    assert bench.algorithmic_bytes("filter", N, S, T) == sum(8 * N + 12 * t for t in T)
+    # the fan reads the coordinates of the octagon survivors of the sets it ran on
+    assert bench.algorithmic_bytes("kgon", N, S, T) == 8 * (S[1] + S[2])
+    assert bench.algorithmic_bytes("sort_pass", N, S, T) == sum(4 * 24 * t for t in T)
+    assert bench.algorithmic_bytes("chain", N, S, T) == sum(12 * t for t in T)
+    assert bench.algorithmic_bytes("emit", N, S, T) is None
+
+
+@pytest.fixture
+def one_device(monkeypatch):
+    class Props:
+        multi_processor_count = 152
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: Props())
+
+
+def test_alu_roofline_counts_fan_sets_only(one_device):
+    rec = bench.load_traffic("kgon")
+    assert rec is not None, "profiles/traffic.json must describe the current kgon.cu"
+    steps, launches, ms = 5, 60, 6.0
+    r = bench.alu_roofline(ms, launches, steps, N, S, T, {"sm_max_mhz": 2070.0}, None)
+    inst = rec["warp_inst_per_survivor"] * (S[1] + S[2]) * steps
+    assert r["bound"] == "alu" and r["kernel"] == "kgon"
+    assert r["peak"] == pytest.approx(152 * 4 * 2070e6 / 1e12, abs=1e-3)
+    assert r["achieved"] == pytest.approx(inst / (ms * 1e-3) / 1e12, abs=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], abs=1e-3)
+    assert r["warp_instr_per_launch"] == int(inst / launches)
+
+
+def test_alu_roofline_void_when_source_changed(one_device, monkeypatch):
+    rec = copy.deepcopy(json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json"))))
+    rec["kgon"]["source_sha"] = "0" * 16
+    real_load = json.load
+    monkeypatch.setattr(bench.json, "load", lambda f: rec if f.name.endswith("traffic.json") else real_load(f))
+    assert bench.load_traffic("kgon") is None
+    assert bench.alu_roofline(6.0, 60, 5, N, S, T, {"sm_max_mhz": 2070.0}, None) is None
