@@ -54,8 +54,9 @@ def parse():
                     help="subset of the workload's distributions (profiling runs)")
     ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
                     help="compaction schedule: 0 two passes, 1 single pass with look-back")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
-                    help="single: the three 1e8 sets; batched: 4096 uneven sets, batched call vs per-set calls")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "prior-art"],
+                    help="single: the three 1e8 sets; batched: 4096 uneven sets, batched call vs per-set calls; "
+                         "prior-art: extremes + filter against the paper's Thrust/CUB variants (context)")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     return ap.parse_args()
 
@@ -541,11 +542,97 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+PRIOR_VARIANTS = ("cub-flagged", "thrust-copy", "thrust-scan")
+
+
+def run_prior_art(args):
+    """Context for the paper's library variants (Sec. 4): each set's extremes
+    + filter + compaction done with Thrust / CUB calls (cub-flagged,
+    thrust-copy, thrust-scan, with the paper's plain binary32 point test;
+    libpriorart) against this library's ch_extremes + ch_filter (exact
+    test), on the same resident inputs, CUDA events over the calls."""
+    import ctypes
+
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    from paper_2303_10581_gb300 import build as build_mod
+
+    lib = ctypes.CDLL(build_mod.build_prior_art())
+    lib.pa_workspace_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    lib.pa_filter.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    host = make_inputs(n, args.seed)
+    size = ctypes.c_size_t()
+    assert lib.pa_workspace_size(n, ctypes.byref(size)) == 0
+    pws = torch.empty(size.value, dtype=torch.uint8, device=dev)
+    ws = ch.Workspace(n, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    out_pts = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    ext = torch.zeros(8, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / args.steps
+
+    per_set = {}
+    for k, dist in enumerate(DISTS):
+        d = torch.from_numpy(host[k]).to(dev)
+
+        def ours():
+            ch.ch_extremes(d, ext, ws.buf, stream)
+            ch.ch_filter(d, ext, out, out_pts, cnt, ws.buf, stream)
+
+        row = {"this library": {"ms": round(timed(ours), 4), "survivors": int(cnt.item())}}
+        ws.check()
+        for v, name in enumerate(PRIOR_VARIANTS):
+            def lib_variant(v=v):
+                rc = lib.pa_filter(d.data_ptr(), n, v, out.data_ptr(), cnt.data_ptr(), pws.data_ptr(), size.value,
+                                   stream.cuda_stream)
+                assert rc == 0, (name, rc)
+
+            row[name] = {"ms": round(timed(lib_variant), 4), "survivors": int(cnt.item())}
+        for r in row.values():
+            r["gpoints_s"] = round(n / (r["ms"] * 1e-3) / 1e9, 2)
+        per_set[dist] = row
+        del d
+    ours_ms = sum(per_set[d]["this library"]["ms"] for d in DISTS) / len(DISTS)
+    best_lib = {name: sum(per_set[d][name]["ms"] for d in DISTS) / len(DISTS) for name in PRIOR_VARIANTS}
+    line = {
+        "metric": "extremes + filter + compaction per set: this library vs the paper's Thrust/CUB variants (context)",
+        "value": round(ours_ms, 4), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"one set of n={n} per distribution: " + ", ".join(DISTS), "n_per_set": n,
+                   "note": "library variants use the paper's plain binary32 test, this library the exact one"},
+        "ms_per_set_mean": {"this library": round(ours_ms, 4), **{k: round(v, 4) for k, v in best_lib.items()}},
+        "per_set": per_set,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global DISTS
     args = parse()
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "prior-art":
+        DISTS = tuple(d for d in args.dists.split(",") if d)
+        run_prior_art(args)
         return
     DISTS = tuple(d for d in args.dists.split(",") if d)
     assert DISTS and all(d in ALL_DISTS for d in DISTS), args.dists

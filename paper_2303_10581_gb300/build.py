@@ -17,6 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libconvhull.so")
+# the paper's Thrust / CUB filter variants, for timing context only
+PRIOR_SRC = os.path.join(HERE, "prior_art", "prior_art.cu")
+PRIOR_LIB = os.path.join(OUT_DIR, "libpriorart.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
@@ -45,7 +48,30 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+def build_prior_art(force: bool = False) -> str:
+    """The Thrust / CUB variants library (one translation unit)."""
+    if not force and os.path.exists(PRIOR_LIB) and os.path.getmtime(PRIOR_LIB) >= os.path.getmtime(PRIOR_SRC):
+        return PRIOR_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PRIOR_LIB + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+           PRIOR_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PRIOR_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PRIOR_LIB)
+    return PRIOR_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+    with ThreadPoolExecutor(max_workers=1) as side:   # the slow Thrust/CUB unit alongside
+        prior = side.submit(build_prior_art, force)
+        lib = _build_main(force, verbose, extra_flags)
+        prior.result()
+    return lib
+
+
+def _build_main(force: bool, verbose: bool, extra_flags) -> str:
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
