@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--copy-streams", type=int, default=2, help="host-to-device copy streams of the e2e step")
     ap.add_argument("--dists", default=",".join(ALL_DISTS),
                     help="subset of the workload's distributions (profiling runs)")
     ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
@@ -378,19 +379,21 @@ def run_ours(args):
         out_host = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in DISTS]
         cnt_host = [torch.empty(1, dtype=torch.int32).pin_memory() for _ in DISTS]
 
-        # copies and hulls overlap: every set's points go up on two copy
-        # streams (halves) while the compute stream works on the previous
-        # set; the set with the shortest hull goes last
-        copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+        # copies and hulls overlap: every set's points go up in equal parts
+        # on several copy streams while the compute stream works on the
+        # previous set; the set with the shortest hull goes last
+        nc = max(1, args.copy_streams)
+        copy_streams = [torch.cuda.Stream(device=dev) for _ in range(nc)]
         order = sorted(range(len(DISTS)), key=lambda k: -sum(per_set[DISTS[k]].values()))
-        half = n // 2
+        cuts = [n * c // nc for c in range(nc + 1)]
 
         def e2e_step():
             d2h = 0
             ready = []
             for k in order:
                 evs = []
-                for c, (lo, hi) in enumerate(((0, half), (half, n))):
+                for c in range(nc):
+                    lo, hi = cuts[c], cuts[c + 1]
                     with torch.cuda.stream(copy_streams[c]):
                         d_pts[k][lo:hi].copy_(pinned[k][lo:hi], non_blocking=True)
                         ev = torch.cuda.Event()
