@@ -22,8 +22,8 @@
 // tile's inverse permutation at write-out, so it never occupies registers.
 // When a block takes a ticket it also asks the TMA unit to bring the tile
 // one grid ahead into L2 (tickets go out in order, so that tile is taken
-// about one tile-time later).  The survivors come from the buffer the hull
-// step left them in (ctrl->sort_in: 0, or 1 after its second polygon).
+// about one tile-time later).  The survivors come from the buffer
+// ctrl->sort_in names (the filter writes buffer 0).
 #include <algorithm>
 
 #include "common.cuh"
