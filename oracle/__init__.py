@@ -67,6 +67,10 @@ def _load():
         lib.oracle_keep_flags.argtypes = [p, ctypes.c_int64, p, p, ctypes.c_int64, p]
         lib.oracle_keep_flags.restype = ctypes.c_int
         lib.oracle_hull.argtypes = [p, p, ctypes.c_int64, p]
+        lib.oracle_kgon_extremes.argtypes = [p, ctypes.c_int64, ctypes.c_int, p, p]
+        lib.oracle_kgon_extremes.restype = ctypes.c_int
+        lib.oracle_kgon_filter.argtypes = [p, ctypes.c_int64, ctypes.c_int, p, p]
+        lib.oracle_kgon_filter.restype = ctypes.c_int64
         lib.oracle_hull.restype = ctypes.c_int64
         _lib = lib
     return _lib
@@ -167,6 +171,33 @@ def hull(points, idx=None) -> np.ndarray:
     if h < 0:
         raise OracleError(int(h), "hull")
     return out[:h].copy()
+
+
+def kgon_extremes(points, dirs) -> np.ndarray:
+    """Vertex k of the K-direction polygon: argmax of fl(fl(c_k x) + fl(s_k y))
+    over the points, lowest index on ties; dirs is (K, 2) binary32."""
+    p = _pts(points)
+    d = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 2)
+    out = np.zeros(d.shape[0], dtype=np.uint32)
+    rc = _load().oracle_kgon_extremes(_ptr(p), p.shape[0], d.shape[0], _ptr(d), _ptr(out))
+    if rc != OK:
+        raise OracleError(rc, "kgon_extremes")
+    return out
+
+
+def kgon_filter(points, dirs, ext=None) -> np.ndarray:
+    """Ascending indices of the points not strictly inside the K-vertex
+    polygon of the directions dirs (or of the vertices ext)."""
+    p = _pts(points)
+    n = p.shape[0]
+    if n == 0:
+        return np.zeros(0, dtype=np.uint32)
+    e = kgon_extremes(p, dirs) if ext is None else np.ascontiguousarray(ext, dtype=np.uint32)
+    out = np.empty(n, dtype=np.uint32)
+    s = _load().oracle_kgon_filter(_ptr(p), n, e.shape[0], _ptr(e), _ptr(out))
+    if s < 0:
+        raise OracleError(int(s), "kgon_filter")
+    return out[:s].copy()
 
 
 def convex_hull(points):

@@ -260,6 +260,74 @@ int oracle_keep_flags(const float *pts, int64_t n, const uint32_t *ext8, const u
 }
 
 /* ------------------------------------------------------------------ */
+/* K directions: the filter polygon of the learned proposal            */
+/* ------------------------------------------------------------------ */
+
+/* The polygon generalised from the eight directions of Sec. 3.1 to K
+ * directions (c_k, s_k), k = 0 .. K-1 (dirs holds them as pairs, in
+ * counter-clockwise order; |c_k|, |s_k| <= 1): vertex k is the point with
+ * the largest binary32 key fl(fl(c_k x) + fl(s_k y)), ties to the lowest
+ * index.  With the eight integer directions (1,0), (1,1), (0,1), (-1,1),
+ * (-1,0), (-1,-1), (0,-1), (1,-1) the keys are x, fl(x+y), y, -fl(x-y), -x,
+ * -fl(x+y), -y, fl(x-y) and the vertices are the octagon's R ... BR.
+ * ext receives K indices.  Returns OR_ERR_NONFINITE for a NaN or infinite
+ * coordinate. */
+int oracle_kgon_extremes(const float *pts, int64_t n, int K, const float *dirs, uint32_t *ext)
+{
+    if (n < 1 || K < 3 || K > 64 || !pts || !dirs || !ext) return OR_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (!finite_point(pts[2 * i], pts[2 * i + 1])) return OR_ERR_NONFINITE;
+    for (int k = 0; k < K; ++k) {
+        const float c = dirs[2 * k], sn = dirs[2 * k + 1];
+        float best = c * pts[0] + sn * pts[1];
+        uint32_t at = 0;
+        for (int64_t i = 1; i < n; ++i) {
+            const float key = c * pts[2 * i] + sn * pts[2 * i + 1];
+            if (key > best) {
+                best = key;
+                at = (uint32_t)i;
+            }
+        }
+        ext[k] = at;
+    }
+    return OR_OK;
+}
+
+/* 1 if the point must be kept: not strictly to the left of every edge of
+ * non-zero length of the closed vertex sequence v[0 .. K-1]. */
+static int keep_point_k(const float *v, int K, float px, float py)
+{
+    int edges = 0;
+    for (int k = 0; k < K; ++k) {
+        float ax = v[2 * k], ay = v[2 * k + 1];
+        float bx = v[2 * ((k + 1) % K)], by = v[2 * ((k + 1) % K) + 1];
+        if (ax == bx && ay == by) continue;
+        ++edges;
+        if (oracle_orient(ax, ay, bx, by, px, py) <= 0) return 1;
+    }
+    return edges == 0;
+}
+
+/* Ascending indices of the points kept by the K-vertex polygon
+ * pts[ext[0]], ..., pts[ext[K-1]]; returns their number, or -1 on bad
+ * arguments. */
+int64_t oracle_kgon_filter(const float *pts, int64_t n, int K, const uint32_t *ext, uint32_t *surv_idx)
+{
+    if (n < 0 || K < 3 || K > 64 || (n > 0 && (!pts || !ext || !surv_idx))) return -1;
+    if (n == 0) return 0;
+    float v[128];
+    for (int k = 0; k < K; ++k) {
+        if ((int64_t)ext[k] >= n) return -1;
+        v[2 * k] = pts[2 * (int64_t)ext[k]];
+        v[2 * k + 1] = pts[2 * (int64_t)ext[k] + 1];
+    }
+    int64_t s = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (keep_point_k(v, K, pts[2 * i], pts[2 * i + 1])) surv_idx[s++] = (uint32_t)i;
+    return s;
+}
+
+/* ------------------------------------------------------------------ */
 /* Sec. 3.3: Andrew's monotone chain                                   */
 /* ------------------------------------------------------------------ */
 

@@ -113,3 +113,31 @@ def lattice_circle(radius: int) -> np.ndarray:
                 pts.append((x, -y))
                 pts.append((x, y))
     return np.array(pts, dtype=np.float32).reshape(-1, 2)
+
+
+# the eight integer directions of the octagon, counter-clockwise from +x
+_OCTAGON_DIRS = ((1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1))
+
+
+def kgon_directions(K: int, offsets=None) -> np.ndarray:
+    """(K, 2) binary32 directions (c_k, s_k) at the angles 2 pi k / K + off_k,
+    counter-clockwise: an input of the K-direction filter polygon (the
+    parameters a learned proposal would choose).  cos and sin are taken in
+    binary64 and rounded once; an angle that is a multiple of pi/4 with zero
+    offset gets the octagon's integer direction instead, so K = 8 without
+    offsets gives the octagon's keys exactly."""
+    off = np.zeros(K) if offsets is None else np.asarray(offsets, dtype=np.float64)
+    out = np.empty((K, 2), dtype=np.float32)
+    for k in range(K):
+        if off[k] == 0.0 and (8 * k) % K == 0:
+            out[k] = _OCTAGON_DIRS[8 * k // K]
+        else:
+            th = 2.0 * math.pi * k / K + float(off[k])
+            out[k] = (math.cos(th), math.sin(th))
+    return out
+
+
+def kgon_offsets(K: int, seed: int, spread: float = 0.45) -> np.ndarray:
+    """Random angular offsets in (-spread, spread) * pi / K: the directions
+    stay in counter-clockwise order."""
+    return (_rng(seed).uniform(-spread, spread, K) * math.pi / K).astype(np.float64)
