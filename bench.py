@@ -55,9 +55,10 @@ def parse():
                     help="subset of the workload's distributions (profiling runs)")
     ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
                     help="compaction schedule: 0 two passes, 1 single pass with look-back")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "prior-art"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "prior-art", "kgon"],
                     help="single: the three 1e8 sets; batched: 4096 uneven sets, batched call vs per-set calls; "
-                         "prior-art: extremes + filter against the paper's Thrust/CUB variants (context)")
+                         "prior-art: extremes + filter against the paper's Thrust/CUB variants (context); "
+                         "kgon: K-direction filter polygons against the octagon")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     return ap.parse_args()
 
@@ -627,6 +628,89 @@ def run_prior_art(args):
     print(json.dumps(line), flush=True)
 
 
+KGON_KS = (8, 16, 32, 64)
+
+
+def run_kgon(args):
+    """The K-direction filter polygon against the plain octagon, on the
+    same resident sets: the filter stage (extremes + test + compaction of
+    indices and points) and the end-to-end hull, ms per set by CUDA events,
+    with the survivors of each polygon -- the timings a learned proposal of
+    K would be trained on.  Directions: angles 2 pi k / K, no offsets."""
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    import pointgen
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    host = make_inputs(n, args.seed)
+    ws = ch.Workspace(n, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    out_pts = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    ext = torch.zeros(64, dtype=torch.int32, device=dev)
+    dirs = {K: torch.from_numpy(pointgen.kgon_directions(K)).to(dev) for K in KGON_KS}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return round(t0.elapsed_time(t1) / args.steps, 4)
+
+    per_set = {}
+    for k, dist in enumerate(DISTS):
+        d = torch.from_numpy(host[k]).to(dev)
+        row = {}
+
+        def oct_filter():
+            ch.ch_extremes(d, ext[:8], ws.buf, stream)
+            ch.ch_filter(d, ext[:8], out, out_pts, cnt, ws.buf, stream)
+
+        def oct_hull():
+            ch.ch_hull(d, out, cnt, ws.buf, stream)
+
+        f_ms = timed(oct_filter)
+        s = int(cnt.item())
+        h_ms = timed(oct_hull)
+        row["octagon"] = {"filter_ms": f_ms, "survivors": s, "hull_ms": h_ms, "hull": int(cnt.item()),
+                          "hull_note": "ch_hull: octagon filter, fan test, sort, chain"}
+        for K in KGON_KS:
+            def kf(K=K):
+                ch.ch_filter_kgon(d, dirs[K], ext[:K], out, out_pts, cnt, ws.buf, stream)
+
+            def kh(K=K):
+                ch.ch_hull_kgon(d, dirs[K], out, cnt, ws.buf, stream)
+
+            f_ms = timed(kf)
+            s = int(cnt.item())
+            h_ms = timed(kh)
+            row[f"K={K}"] = {"filter_ms": f_ms, "survivors": s, "hull_ms": h_ms, "hull": int(cnt.item())}
+        ws.check()
+        per_set[dist] = row
+        del d
+    line = {
+        "metric": "K-direction filter polygon vs the octagon: filter-stage and end-to-end hull ms per set",
+        "value": round(sum(per_set[d]["octagon"]["hull_ms"] for d in DISTS) / len(DISTS), 4), "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "dtype": "f32+exact", "data": "synthetic",
+        "config": {"workload": f"one set of n={n} per distribution: " + ", ".join(DISTS), "n_per_set": n,
+                   "directions": "angles 2 pi k / K, axis and diagonal keys as the octagon's",
+                   "note": "ch_hull_kgon sorts every survivor of its polygon (no fan test)"},
+        "per_set": per_set,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global DISTS
     args = parse()
@@ -636,6 +720,10 @@ def main():
     if args.workload == "prior-art":
         DISTS = tuple(d for d in args.dists.split(",") if d)
         run_prior_art(args)
+        return
+    if args.workload == "kgon":
+        DISTS = tuple(d for d in args.dists.split(",") if d)
+        run_kgon(args)
         return
     DISTS = tuple(d for d in args.dists.split(",") if d)
     assert DISTS and all(d in ALL_DISTS for d in DISTS), args.dists

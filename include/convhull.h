@@ -113,6 +113,29 @@ ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_
                           uint32_t *hull_idx, int64_t *hull_offsets,
                           void *ws, size_t ws_bytes, void *stream);
 
+/* The filter polygon generalised to K directions (the polygon a learned
+ * proposal picks; Sec. 3.1-3.2 with K in place of 8).  dirs is a DEVICE
+ * array of K (c_k, s_k) binary32 pairs, counter-clockwise, |c_k|, |s_k| <= 1;
+ * K is 8, 16, 32 or 64 (CH_ERR_ARG otherwise).  Vertex k is the point with
+ * the largest key fl(fl(c_k x) + fl(s_k y)) (binary32, lowest index on
+ * ties); with the eight directions (1,0), (1,1), (0,1), (-1,1), (-1,0),
+ * (-1,-1), (0,-1), (1,-1) these are the octagon's keys and vertices.  A
+ * point is discarded when it is strictly left of every edge of non-zero
+ * length of the closed vertex sequence (exact sign); the kept points are
+ * compacted as by ch_filter (surv_idx ascending, surv_pts may be NULL,
+ * *surv_count on the device).  ext_out (device, K entries, may be NULL)
+ * receives the vertex indices.  Non-finite input: CH_ERR_NONFINITE in ws,
+ * zero count.  Not part of the paper's method: its generalisation. */
+ch_status ch_filter_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *ext_out,
+                         uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* ch_hull with the K-direction polygon of ch_filter_kgon as its filter
+ * (same hull: every polygon vertex is an input point).  The hull step
+ * sorts and chains every survivor (no fan test). */
+ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *hull_idx,
+                       uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
+
 /* Waits for `stream`, then returns and clears the first device-side error
  * recorded in ws since the last call (CH_OK if none). */
 ch_status ch_last_error(void *ws, void *stream);

@@ -32,7 +32,7 @@ CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOU
 
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
-           "ch_filter_variant", "ch_hull_counts")
+           "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
@@ -74,6 +74,8 @@ def load(build_if_missing: bool = True):
     lib.ch_filter_noalloc.argtypes = [p, i64, p, p, p, p, p]
     lib.ch_filter_variant.argtypes = [ctypes.c_int32]
     lib.ch_hull_counts.argtypes = [p, sz, i64, p, p]
+    lib.ch_filter_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, p, p, sz, p]
+    lib.ch_hull_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, sz, p]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -139,6 +141,20 @@ def ch_hull(pts, hull_idx, hull_count, ws, stream=None):
     _check(load().ch_hull(_ptr(pts, "pts"), pts.shape[0], _ptr(hull_idx, "hull_idx"),
                           _ptr(hull_count, "hull_count"), _ptr(ws, "ws"), ws.numel(), _stream(stream)),
            "ch_hull")
+
+
+def ch_filter_kgon(pts, dirs, ext_out, surv_idx, surv_pts, surv_count, ws, stream=None):
+    """K-direction filter polygon; dirs is a (K, 2) float32 CUDA tensor."""
+    _check(load().ch_filter_kgon(_ptr(pts, "pts"), pts.shape[0], _ptr(dirs, "dirs"), dirs.shape[0],
+                                 _ptr(ext_out, "ext_out"), _ptr(surv_idx, "surv_idx"), _ptr(surv_pts, "surv_pts"),
+                                 _ptr(surv_count, "surv_count"), _ptr(ws, "ws"), ws.numel(), _stream(stream)),
+           "ch_filter_kgon")
+
+
+def ch_hull_kgon(pts, dirs, hull_idx, hull_count, ws, stream=None):
+    _check(load().ch_hull_kgon(_ptr(pts, "pts"), pts.shape[0], _ptr(dirs, "dirs"), dirs.shape[0],
+                               _ptr(hull_idx, "hull_idx"), _ptr(hull_count, "hull_count"), _ptr(ws, "ws"),
+                               ws.numel(), _stream(stream)), "ch_hull_kgon")
 
 
 def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):
@@ -244,6 +260,41 @@ def convex_hull(pts, ws: Workspace | None = None):
     idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
     cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
     ch_hull(pts, idx, cnt, ws.buf)
+    return idx, cnt
+
+
+def _as_dirs(dirs, device):
+    import torch
+    d = torch.as_tensor(dirs, dtype=torch.float32).reshape(-1, 2)
+    return d.to(device).contiguous()
+
+
+def filter_points_kgon(pts, dirs, ws: Workspace | None = None):
+    """(vertex indices, surv_idx, surv_pts, count) on the device for the
+    K-direction polygon of the (K, 2) directions ``dirs``."""
+    import torch
+    pts = _as_points(pts)
+    n = pts.shape[0]
+    d = _as_dirs(dirs, pts.device)
+    ws = ws or Workspace(n, device=pts.device)
+    ext = torch.zeros(d.shape[0], dtype=torch.int32, device=pts.device)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+    sp = torch.empty((max(n, 1), 2), dtype=torch.float32, device=pts.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
+    ch_filter_kgon(pts, d, ext, idx, sp, cnt, ws.buf)
+    return ext, idx, sp, cnt
+
+
+def convex_hull_kgon(pts, dirs, ws: Workspace | None = None):
+    """(hull_idx, count) on the device, with the K-direction filter polygon."""
+    import torch
+    pts = _as_points(pts)
+    n = pts.shape[0]
+    d = _as_dirs(dirs, pts.device)
+    ws = ws or Workspace(n, device=pts.device)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
+    ch_hull_kgon(pts, d, idx, cnt, ws.buf)
     return idx, cnt
 
 

@@ -73,6 +73,60 @@ extern "C" ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8
     return cuda_status(launch_filter(pts, n, ws, L, surv_idx, surv_pts, surv_count, false, st));
 }
 
+namespace {
+
+inline bool kgon_k_ok(int32_t K) { return K == 8 || K == 16 || K == 32 || K == 64; }
+
+}  // namespace
+
+extern "C" ch_status ch_filter_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *ext_out,
+                                    uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count, void *ws,
+                                    size_t ws_bytes, void *stream)
+{
+    if (!surv_count || n < 0 || !aligned(surv_count, 4) || !kgon_k_ok(K)) return CH_ERR_ARG;
+    if (n > kMaxN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(surv_count, 0, sizeof(uint32_t), st));
+    if (!pts || !dirs || !surv_idx || !aligned(pts, 8) || !aligned(dirs, 4) || !aligned(surv_idx, 4) ||
+        (surv_pts && !aligned(surv_pts, 8)) || (ext_out && !aligned(ext_out, 4)))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    int64_t grid = 0;
+    cudaError_t e = launch_kx_extremes(pts, n, dirs, K, ext_out, ws, L, st);
+    if (e == cudaSuccess) e = launch_kx_count(pts, n, K, ws, L, &grid, st);
+    if (e == cudaSuccess) {
+        probe_before(CH_K_FILTER, st);
+        e = launch_filter_scatter(pts, n, grid, ws, L, surv_idx, surv_pts, surv_count, false, st);
+        probe_after(CH_K_FILTER, st);
+    }
+    return cuda_status(e);
+}
+
+extern "C" ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *hull_idx,
+                                  uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!hull_count || n < 0 || !aligned(hull_count, 4) || !kgon_k_ok(K)) return CH_ERR_ARG;
+    if (n >= kMaxHullN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(hull_count, 0, sizeof(uint32_t), st));
+    if (!pts || !dirs || !hull_idx || !aligned(pts, 8) || !aligned(dirs, 4) || !aligned(hull_idx, 4))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    int64_t grid = 0;
+    cudaError_t e = launch_kx_extremes(pts, n, dirs, K, nullptr, ws, L, st);
+    if (e == cudaSuccess) e = launch_kx_count(pts, n, K, ws, L, &grid, st);
+    if (e == cudaSuccess) {
+        probe_before(CH_K_FILTER, st);
+        e = launch_filter_scatter(pts, n, grid, ws, L, nullptr, nullptr, nullptr, true, st);
+        probe_after(CH_K_FILTER, st);
+    }
+    if (e == cudaSuccess) e = launch_sort(ws, L, st);
+    if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
+    return cuda_status(e);
+}
+
 extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
                              size_t ws_bytes, void *stream)
 {

@@ -98,6 +98,25 @@ struct Kgon {
     float2 v[kFanBins];                    // vertex of every bin (input points)
 };
 
+// K-direction filter polygon (kfilter.cu; the learned proposal's filter)
+constexpr int kMaxDirs = 64;
+
+struct KxCtrl {                            // left zeroed by the last block of every sweep
+    unsigned long long slot[kMaxDirs];     // packed (ord(key) << 32 | ~index) per direction
+    uint32_t done;                         // sweep blocks finished
+    uint32_t nonfinite;                    // a non-finite coordinate was seen
+};
+
+struct KPoly {
+    uint32_t K;
+    uint32_t nvalid;                       // edges of non-zero length
+    unsigned long long valid;              // bit k: edge k (vertex k -> k+1) has non-zero length
+    float xl, xh, yl, yh;                  // closed quick-discard rectangle (xl > xh: none)
+    float cx, cy;                          // vertex bounding-box centre (facing-edge hint)
+    float ax[kMaxDirs], ay[kMaxDirs];      // edge k: vertex k ...
+    float bx[kMaxDirs], by[kMaxDirs];      // ... to vertex k + 1
+};
+
 // control block: zeroed at the start of every call (together with the
 // filter's look-back status, which follows it)
 struct Ctrl {
@@ -125,6 +144,7 @@ struct Persist {
 // Workspace layout for a problem of up to n points.
 struct Layout {
     size_t persist, extctrl, oct, ext8;
+    size_t kxctrl, kpoly;   // KxCtrl (self-resetting), KPoly
     size_t ctrl;            // Ctrl, immediately followed by
     size_t filt_status;     // u64[filt_tiles],
     size_t kgon_ctrl;       // KgonCtrl,
@@ -232,6 +252,8 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.extctrl = take(sizeof(ExtCtrl));
     L.oct = take(sizeof(Octagon));
     L.ext8 = take(8 * sizeof(uint32_t));
+    L.kxctrl = take(sizeof(KxCtrl));
+    L.kpoly = take(sizeof(KPoly));
     L.ctrl = take(sizeof(Ctrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
     L.kgon_ctrl = take(sizeof(KgonCtrl));

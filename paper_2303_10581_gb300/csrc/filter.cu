@@ -855,6 +855,24 @@ cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L
                : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false);
 }
 
+cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, void *ws, const Layout &L,
+                                  uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count, bool keys_mode,
+                                  cudaStream_t st)
+{
+    const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
+    float2 *sp = reinterpret_cast<float2 *>(surv_pts);
+    const unsigned g = (unsigned)std::max<int64_t>(1, grid);
+    if (keys_mode) {
+        if (vec) filter_scatter_kernel<2, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr);
+        else filter_scatter_kernel<1, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr);
+    } else {
+        if (vec) filter_scatter_kernel<2, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count);
+        else filter_scatter_kernel<1, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count);
+    }
+    note_kernels(CH_K_FILTER, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
 {
     static int per_sm_c = occupancy(bx_filter_count_kernel, kFiltThreads);

@@ -1,0 +1,397 @@
+// kfilter.cu -- the filter polygon generalised from the eight directions of
+// Sec. 3.1 to K in {8, 16, 32, 64} directions: the polygon a learned
+// proposal picks (the paper's related work cites a 16-direction filter as
+// precedent).
+//
+// The directions (c_k, s_k) come from the caller (device array, counter-
+// clockwise, |c_k|, |s_k| <= 1).  Vertex k is the point with the largest
+// binary32 key fl(fl(c_k x) + fl(s_k y)), lowest index on ties; with the
+// octagon's eight integer directions (1,0), (1,1), (0,1), (-1,1), ... these
+// are exactly the keys of Sec. 3.1.  A point is discarded when it is
+// strictly left of every edge of non-zero length of the closed vertex
+// sequence (exact signs), as in Sec. 3.2; the vertices are input points, so
+// no hull vertex is ever discarded.
+//
+//  kx_extremes_kernel<K>  tiles of 1024 points staged in shared memory;
+//                         thread t keeps the best point of direction t mod K
+//                         over its share of each tile; per-direction packed
+//                         atomicMax (ord(key) << 32 | ~index); the last block
+//                         decodes, resets the slots and builds the polygon
+//                         (edges, an exact quick-discard rectangle)
+//  kx_count_kernel<G>     the filter's count pass with this polygon: the
+//                         rectangle, then the edges starting at the one
+//                         facing the point; keep bits, tile counts and block
+//                         totals in the filter's layout, so its scatter pass
+//                         compacts the survivors
+#include <algorithm>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace ch {
+namespace {
+
+constexpr int XT = 512;       // threads per block of the sweep
+constexpr int XTILE = 1024;   // points per tile of the sweep
+constexpr uint32_t kSiteKxNonFinite = 50;
+
+// Larger key, or equal key and lower index; index 0xffffffff: no candidate.
+__device__ __forceinline__ void take_better(float &k, uint32_t &i, float ok, uint32_t oi)
+{
+    if (oi == 0xffffffffu) return;
+    if (i == 0xffffffffu || ok > k || (ok == k && oi < i)) {
+        k = ok;
+        i = oi;
+    }
+}
+
+// Last block: the polygon from the decoded vertices.  The rectangle is
+// accepted when its four corners are strictly left of every edge of non-zero
+// length (exact signs): that region is an intersection of open half-planes,
+// hence convex, so the whole closed rectangle lies in it.
+__device__ void build_kpoly(const float2 *p, int K, const uint32_t *s_ext, KPoly *kp)
+{
+    __shared__ float s_vx[kMaxDirs], s_vy[kMaxDirs];
+    __shared__ unsigned s_vm[2];
+    __shared__ float s_box[4];
+    const int t = (int)threadIdx.x;
+    if (t < K) {
+        const float2 v = p[s_ext[t]];
+        s_vx[t] = v.x;
+        s_vy[t] = v.y;
+    }
+    __syncthreads();
+    bool valid = false;
+    if (t < K) {
+        const int kn = t + 1 == K ? 0 : t + 1;
+        const float ax = s_vx[t], ay = s_vy[t], bx = s_vx[kn], by = s_vy[kn];
+        valid = !(ax == bx && ay == by);
+        kp->ax[t] = ax;
+        kp->ay[t] = ay;
+        kp->bx[t] = bx;
+        kp->by[t] = by;
+    }
+    if (t < 64) {
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if ((t & 31) == 0) s_vm[t >> 5] = m;
+    }
+    if (t == 0) {
+        float x0 = s_vx[0], x1 = s_vx[0], y0 = s_vy[0], y1 = s_vy[0];
+        for (int k = 1; k < K; ++k) {
+            x0 = fminf(x0, s_vx[k]);
+            x1 = fmaxf(x1, s_vx[k]);
+            y0 = fminf(y0, s_vy[k]);
+            y1 = fmaxf(y1, s_vy[k]);
+        }
+        s_box[0] = x0;
+        s_box[1] = x1;
+        s_box[2] = y0;
+        s_box[3] = y1;
+    }
+    __syncthreads();
+    const unsigned long long vmask = (unsigned long long)s_vm[0] | ((unsigned long long)s_vm[1] << 32);
+    const unsigned long long kmask = K == 64 ? ~0ull : ((1ull << K) - 1ull);
+    const unsigned long long valid_mask = vmask & kmask;
+    const double cxd = 0.5 * ((double)s_box[0] + (double)s_box[1]);
+    const double cyd = 0.5 * ((double)s_box[2] + (double)s_box[3]);
+    const double hw = 0.5 * ((double)s_box[1] - (double)s_box[0]);
+    const double hh = 0.5 * ((double)s_box[3] - (double)s_box[2]);
+    float xl = 1.0f, xh = -1.0f, yl = 1.0f, yh = -1.0f;   // empty
+    if (valid_mask != 0ull) {
+        const double fr[8] = {0.90, 0.84, 0.78, 0.70, 0.60, 0.48, 0.35, 0.22};
+        for (int j = 0; j < 8; ++j) {
+            const float rxl = (float)(cxd - fr[j] * hw), rxh = (float)(cxd + fr[j] * hw);
+            const float ryl = (float)(cyd - fr[j] * hh), ryh = (float)(cyd + fr[j] * hh);
+            bool ok = rxl <= rxh && ryl <= ryh;
+            if (t < 4 * K) {   // corner t / K against edge t % K
+                const int c = t / K, e = t % K, en = e + 1 == K ? 0 : e + 1;
+                const float px = (c == 0 || c == 3) ? rxl : rxh;
+                const float py = (c < 2) ? ryl : ryh;
+                if ((valid_mask >> e) & 1ull) ok = ok && orient(s_vx[e], s_vy[e], s_vx[en], s_vy[en], px, py) > 0;
+            }
+            if (__syncthreads_and(ok)) {
+                xl = rxl;
+                xh = rxh;
+                yl = ryl;
+                yh = ryh;
+                break;
+            }
+        }
+    }
+    if (t == 0) {
+        kp->K = (uint32_t)K;
+        kp->nvalid = (uint32_t)__popcll(valid_mask);
+        kp->valid = valid_mask;
+        kp->xl = xl;
+        kp->xh = xh;
+        kp->yl = yl;
+        kp->yh = yh;
+        kp->cx = (float)cxd;
+        kp->cy = (float)cyd;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(XT) kx_extremes_kernel(const float *__restrict__ pts, int64_t n,
+                                                         const float *__restrict__ dirs, uint32_t *ext_out, void *ws,
+                                                         Layout L, unsigned long long *zero_ptr, int64_t zero_words)
+{
+    static_assert(K >= 8 && K <= kMaxDirs && XT % K == 0, "directions split the block evenly");
+    constexpr int PARTS = XT / K;
+    __shared__ float2 s_p[XTILE];
+    __shared__ float s_bk[XT];
+    __shared__ uint32_t s_bi[XT];
+    __shared__ uint32_t s_ext[kMaxDirs];
+    __shared__ int s_nf;
+    __shared__ int s_last;
+    KxCtrl *kc = at<KxCtrl>(ws, L.kxctrl);
+    // clear what the following kernels of this call expect to be zero
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = gtid; w < zero_words; w += gthreads) zero_ptr[w] = 0ull;
+
+    const int d = (int)threadIdx.x % K, part = (int)threadIdx.x / K;
+    const float c = dirs[2 * d], sn = dirs[2 * d + 1];
+    float best = __int_as_float(0x7fc00000);   // NaN: no candidate yet
+    uint32_t bi = 0xffffffffu;
+    float nf = 0.0f;                           // becomes NaN iff a coordinate is NaN or infinite
+    const float2 *p2 = reinterpret_cast<const float2 *>(pts);
+    const int64_t ntiles = ceil_div(n, (int64_t)XTILE);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * XTILE;
+        const int cnt = (int)std::min<int64_t>(XTILE, n - base);
+        for (int j = (int)threadIdx.x; j < XTILE; j += XT) {
+            float2 v = make_float2(0.0f, 0.0f);
+            if (j < cnt) {
+                v = __ldcs(p2 + base + j);
+                nf = __fmaf_rn(v.x, 0.0f, nf);
+                nf = __fmaf_rn(v.y, 0.0f, nf);
+            }
+            s_p[j] = v;
+        }
+        __syncthreads();
+        for (int q = part; q < cnt; q += PARTS) {
+            const float2 v = s_p[q];
+            const float key = __fadd_rn(__fmul_rn(c, v.x), __fmul_rn(sn, v.y));
+            // the first key is always taken (best starts as NaN); then only
+            // a strictly larger one, so ties keep the lower index
+            if (!(key <= best)) {
+                best = key;
+                bi = (uint32_t)(base + q);
+            }
+        }
+        __syncthreads();
+    }
+    s_bk[threadIdx.x] = best;
+    s_bi[threadIdx.x] = bi;
+    if (threadIdx.x == 0) s_nf = 0;
+    __syncthreads();
+    if (nf != nf) s_nf = 1;
+    if ((int)threadIdx.x < K) {
+        float k = s_bk[threadIdx.x];
+        uint32_t i = s_bi[threadIdx.x];
+        for (int pp = 1; pp < PARTS; ++pp) take_better(k, i, s_bk[threadIdx.x + pp * K], s_bi[threadIdx.x + pp * K]);
+        if (i != 0xffffffffu) atomicMax(&kc->slot[threadIdx.x], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_nf) atomicOr(&kc->nonfinite, 1u);
+        __threadfence();
+        s_last = atomicAdd(&kc->done, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // last block: decode, reset the slots for the next call, build the polygon
+    __threadfence();
+    if ((int)threadIdx.x < K) {
+        const unsigned long long packed = atomicExch(&kc->slot[threadIdx.x], 0ull);
+        uint32_t idx = ~(uint32_t)packed;
+        if ((int64_t)idx >= n) idx = 0;   // every direction has a candidate; guards the loads below
+        s_ext[threadIdx.x] = idx;
+        if (ext_out) ext_out[threadIdx.x] = idx;
+    }
+    if (threadIdx.x == 0) {
+        s_nf = atomicExch(&kc->nonfinite, 0u) != 0u ? 1 : 0;
+        kc->done = 0;
+    }
+    __syncthreads();
+    Octagon *oct = at<Octagon>(ws, L.oct);
+    if (s_nf) {   // block-uniform
+        if (threadIdx.x == 0) {
+            set_error(ws, L, kErrNonFinite, kSiteKxNonFinite);
+            oct->abort = 1;   // the later kernels of the call do nothing
+        }
+        return;
+    }
+    build_kpoly(p2, K, s_ext, at<KPoly>(ws, L.kpoly));
+    if (threadIdx.x == 0) oct->abort = 0;
+}
+
+// keep(p) <=> NOT (p strictly left of every valid edge).  The edges are
+// tried from the one whose direction range holds p's angle around the
+// centre (a binary32 hint), alternating outwards; the answer does not
+// depend on the order.
+__device__ __forceinline__ bool kx_keep(const KPoly &sp, float x, float y)
+{
+    if (sp.xl <= x && x <= sp.xh && sp.yl <= y && y <= sp.yh) return false;
+    if (sp.nvalid == 0u) return true;
+    const int K = (int)sp.K;
+    const float a = atan2f(y - sp.cy, x - sp.cx);
+    int k0 = (int)floorf(a * ((float)K * 0.15915494f));   // angle / (2 pi / K)
+    k0 = ((k0 % K) + K) % K;
+    for (int j = 0; j < K; ++j) {
+        int k = k0 + ((j & 1) ? -((j + 1) >> 1) : (j >> 1));   // 0, -1, +1, -2, +2, ...
+        k = k < 0 ? k + K : (k >= K ? k - K : k);
+        if (!((sp.valid >> k) & 1ull)) continue;
+        int o = orient_f32(sp.ax[k], sp.ay[k], sp.bx[k], sp.by[k], x, y);
+        if (o == 2) o = orient_rest(sp.ax[k], sp.ay[k], sp.bx[k], sp.by[k], x, y);
+        if (o <= 0) return true;
+    }
+    return false;
+}
+
+// The filter's count pass with the K-gon: each block a contiguous range of
+// 4096-point tiles; thread t's items q = r * G + h are the points
+// base + (r * kFiltThreads + t) * G + h (G = 2: 16-byte point pairs); 16
+// keep bits per thread, the tile's count and the block's total.
+template <int G>
+__global__ void __launch_bounds__(kFiltThreads) kx_count_kernel(const float *__restrict__ pts, int64_t n, void *ws,
+                                                               Layout L)
+{
+    constexpr int ROWS = kFiltItems / G;
+    __shared__ KPoly sp;
+    __shared__ uint32_t s_w[kFiltThreads / 32];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = at<Octagon>(ws, L.oct)->abort ? 1 : 0;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(at<KPoly>(ws, L.kpoly));
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+        for (uint32_t w = threadIdx.x; w < sizeof(KPoly) / 4; w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (s_abort) return;
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t t1 = std::min<int64_t>(ntiles, (int64_t)(blockIdx.x + 1) * per);
+    const uint32_t t = threadIdx.x, warp = t >> 5, lane = lane_id();
+    uint32_t block_total = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
+        const int64_t base = tile * kFiltTile;
+        if (t == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const int64_t nb = base + kFiltTile;
+            const uint32_t nn = (uint32_t)std::min<int64_t>(kFiltTile, n - nb);
+            if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
+        }
+        float px[kFiltItems], py[kFiltItems];
+        uint32_t live = 0;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int64_t i = base + (int64_t)(r * kFiltThreads + t) * G;
+            if constexpr (G == 2) {
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (i + 1 < n) {
+                    v = __ldcs(reinterpret_cast<const float4 *>(pts) + i / 2);
+                    live |= 3u << (2 * r);
+                } else if (i < n) {
+                    const float2 a = reinterpret_cast<const float2 *>(pts)[i];
+                    v = make_float4(a.x, a.y, 0.0f, 0.0f);
+                    live |= 1u << (2 * r);
+                }
+                px[2 * r] = v.x;
+                py[2 * r] = v.y;
+                px[2 * r + 1] = v.z;
+                py[2 * r + 1] = v.w;
+            } else {
+                float2 v = make_float2(0.0f, 0.0f);
+                if (i < n) {
+                    v = __ldcs(reinterpret_cast<const float2 *>(pts) + i);
+                    live |= 1u << r;
+                }
+                px[r] = v.x;
+                py[r] = v.y;
+            }
+        }
+        uint32_t keep = 0;
+#pragma unroll
+        for (int q = 0; q < kFiltItems; ++q)
+            if (((live >> q) & 1u) && kx_keep(sp, px[q], py[q])) keep |= 1u << q;
+        bits[tile * kFiltThreads + t] = (uint16_t)keep;
+        uint32_t c = __popc(keep);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) s_w[warp] = c;
+        __syncthreads();
+        if (t == 0) {
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < kFiltThreads / 32; ++w) tot += s_w[w];
+            status[tile] = tot;
+            block_total += tot;
+        }
+        __syncthreads();
+    }
+    if (t == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = block_total;
+}
+
+template <class Kern>
+int resident(Kern k, int threads)
+{
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, threads, 0);
+    return v > 0 ? v : 1;
+}
+
+template <int K>
+cudaError_t launch_kx_extremes_k(const float *pts, int64_t n, const float *dirs, uint32_t *ext_out, void *ws,
+                                 const Layout &L, cudaStream_t st)
+{
+    static const int per_sm = resident(kx_extremes_kernel<K>, XT);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, (int64_t)XTILE), (int64_t)sm_count() * per_sm));
+    kx_extremes_kernel<K><<<(unsigned)blocks, XT, 0, st>>>(pts, n, dirs, ext_out, ws, L,
+                                                           at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_kx_extremes(const float *pts, int64_t n, const float *dirs, int K, uint32_t *ext_out, void *ws,
+                               const Layout &L, cudaStream_t st)
+{
+    probe_before(CH_K_EXTREMES, st);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (K) {
+    case 8: e = launch_kx_extremes_k<8>(pts, n, dirs, ext_out, ws, L, st); break;
+    case 16: e = launch_kx_extremes_k<16>(pts, n, dirs, ext_out, ws, L, st); break;
+    case 32: e = launch_kx_extremes_k<32>(pts, n, dirs, ext_out, ws, L, st); break;
+    case 64: e = launch_kx_extremes_k<64>(pts, n, dirs, ext_out, ws, L, st); break;
+    default: break;
+    }
+    note_kernels(CH_K_EXTREMES, 1);
+    probe_after(CH_K_EXTREMES, st);
+    return e;
+}
+
+cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const Layout &L, int64_t *grid,
+                            cudaStream_t st)
+{
+    (void)K;   // the polygon in ws carries it
+    const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
+    static const int per_sm2 = resident(kx_count_kernel<2>, kFiltThreads);
+    static const int per_sm1 = resident(kx_count_kernel<1>, kFiltThreads);
+    const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
+    const int64_t bc = std::max<int64_t>(
+        1, std::min<int64_t>({ntiles, (int64_t)sm_count() * (vec ? per_sm2 : per_sm1), (int64_t)kFiltMaxBlocks}));
+    *grid = bc;
+    probe_before(CH_K_FILTER, st);
+    if (vec) kx_count_kernel<2><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    else kx_count_kernel<1><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    note_kernels(CH_K_FILTER, 1);
+    probe_after(CH_K_FILTER, st);
+    return cudaGetLastError();
+}
+
+}  // namespace ch

@@ -33,6 +33,20 @@ cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
                           int variant = -1, bool fan = false);
 
+// the filter's scatter pass alone, on keep bits, tile counts and block
+// totals that a count pass of `grid` blocks (same layout as the filter's)
+// left in ws
+cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, void *ws, const Layout &L,
+                                  uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count, bool keys_mode,
+                                  cudaStream_t st);
+
+// K-direction filter polygon (kfilter.cu): extremes sweep + polygon, then
+// the count pass; returns the count grid through *grid (for the scatter)
+cudaError_t launch_kx_extremes(const float *pts, int64_t n, const float *dirs, int K, uint32_t *ext_out, void *ws,
+                               const Layout &L, cudaStream_t st);
+cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const Layout &L, int64_t *grid,
+                            cudaStream_t st);
+
 // hull step: the fan test applied to the keep bits, tile counts and block
 // totals that the filter's count pass (filter_blocks blocks) left in ws;
 // may do nothing.  vec: the count pass used 16-byte point pairs.

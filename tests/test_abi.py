@@ -76,3 +76,14 @@ def test_batched_host_argument_errors():
     assert lib.ch_hull_batched(8, 8, 4, 16, 8, None, big, None) == ch.CH_ERR_ARG
     assert lib.ch_hull_batched(8, 8, 4, 16, 8, 100, big, None) == ch.CH_ERR_ARG     # ws misaligned
     assert lib.ch_hull_batched(8, 8, 4, 16, 8, 256, 1024, None) == ch.CH_ERR_CAPACITY
+
+
+def test_kgon_entry_points_reject_bad_arguments_on_the_host():
+    lib = ch.load()
+    one = ctypes.c_void_p(256)   # never dereferenced: the checks fail first
+    for K in (0, 7, 12, 128):
+        assert lib.ch_filter_kgon(one, 10, one, K, None, one, None, one, one, 1 << 30, None) == ch.CH_ERR_ARG
+        assert lib.ch_hull_kgon(one, 10, one, K, one, one, one, 1 << 30, None) == ch.CH_ERR_ARG
+    assert lib.ch_filter_kgon(one, 10, None, 16, None, one, None, one, one, 1 << 30, None) == ch.CH_ERR_ARG
+    assert lib.ch_filter_kgon(one, -1, one, 16, None, one, None, one, one, 1 << 30, None) == ch.CH_ERR_ARG
+    assert lib.ch_hull_kgon(one, 10, one, 16, one, None, one, 1 << 30, None) == ch.CH_ERR_ARG
