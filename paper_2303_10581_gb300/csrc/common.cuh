@@ -113,6 +113,8 @@ struct KPoly {
     unsigned long long valid;              // bit k: edge k (vertex k -> k+1) has non-zero length
     float xl, xh, yl, yh;                  // closed quick-discard rectangle (xl > xh: none)
     float cx, cy;                          // vertex bounding-box centre (facing-edge hint)
+    uint32_t convex;                       // every vertex on or left of every valid edge, centre strictly inside
+    uint32_t pad;
     float ax[kMaxDirs], ay[kMaxDirs];      // edge k: vertex k ...
     float bx[kMaxDirs], by[kMaxDirs];      // ... to vertex k + 1
 };

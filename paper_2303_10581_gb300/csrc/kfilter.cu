@@ -118,8 +118,24 @@ __device__ void build_kpoly(const float2 *p, int K, const uint32_t *s_ext, KPoly
             }
         }
     }
+    // convexity: every vertex on or left of every valid edge, and the centre
+    // strictly left of all of them.  Then the vertices lie in every edge's
+    // closed half-plane, the interior of their hull lies in every open one,
+    // and a point strictly inside a triangle (centre, v_k, v_k+1) -- part of
+    // that interior -- is strictly left of every edge.
+    bool conv = valid_mask != 0ull;
+    const float ccx = (float)cxd, ccy = (float)cyd;
+    for (int pr = t; pr < K * (K + 1); pr += (int)blockDim.x) {   // (edge, vertex or centre) pairs
+        const int e = pr / (K + 1), m = pr % (K + 1), en = e + 1 == K ? 0 : e + 1;
+        if (!((valid_mask >> e) & 1ull)) continue;
+        const float qx = m < K ? s_vx[m] : ccx, qy = m < K ? s_vy[m] : ccy;
+        const int o = orient(s_vx[e], s_vy[e], s_vx[en], s_vy[en], qx, qy);
+        if (m < K ? o < 0 : o <= 0) conv = false;
+    }
+    conv = __syncthreads_and(conv) != 0;
     if (t == 0) {
         kp->K = (uint32_t)K;
+        kp->convex = conv ? 1u : 0u;
         kp->nvalid = (uint32_t)__popcll(valid_mask);
         kp->valid = valid_mask;
         kp->xl = xl;
@@ -229,10 +245,19 @@ __global__ void __launch_bounds__(XT) kx_extremes_kernel(const float *__restrict
     if (threadIdx.x == 0) oct->abort = 0;
 }
 
-// keep(p) <=> NOT (p strictly left of every valid edge).  The edges are
-// tried from the one whose direction range holds p's angle around the
-// centre (a binary32 hint), alternating outwards; the answer does not
-// depend on the order.
+__device__ __forceinline__ int sign_exact(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    const int o = orient_f32(ax, ay, bx, by, cx, cy);
+    return o != 2 ? o : orient_rest(ax, ay, bx, by, cx, cy);
+}
+
+// keep(p) <=> NOT (p strictly left of every valid edge).  The edge facing
+// p's angle around the centre (a binary32 hint) is tried first: p not
+// strictly left of it is kept.  For a convex polygon, p strictly inside the
+// triangle (centre, v_k, v_k+1) of that edge or a neighbour is discarded
+// (it is strictly left of every edge).  Otherwise every edge is tried,
+// alternating outwards from the hint; the answer does not depend on the
+// order.
 __device__ __forceinline__ bool kx_keep(const KPoly &sp, float x, float y)
 {
     if (sp.xl <= x && x <= sp.xh && sp.yl <= y && y <= sp.yh) return false;
@@ -241,6 +266,18 @@ __device__ __forceinline__ bool kx_keep(const KPoly &sp, float x, float y)
     const float a = atan2f(y - sp.cy, x - sp.cx);
     int k0 = (int)floorf(a * ((float)K * 0.15915494f));   // angle / (2 pi / K)
     k0 = ((k0 % K) + K) % K;
+    if (sp.convex) {
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j) {   // k0, k0 - 1, k0 + 1
+            int k = k0 + (j == 0 ? 0 : (j == 1 ? -1 : 1));
+            k = k < 0 ? k + K : (k >= K ? k - K : k);
+            if (!((sp.valid >> k) & 1ull)) continue;
+            if (sign_exact(sp.ax[k], sp.ay[k], sp.bx[k], sp.by[k], x, y) <= 0) return true;
+            if (sign_exact(sp.cx, sp.cy, sp.ax[k], sp.ay[k], x, y) > 0 &&
+                sign_exact(sp.bx[k], sp.by[k], sp.cx, sp.cy, x, y) > 0)
+                return false;
+        }
+    }
     for (int j = 0; j < K; ++j) {
         int k = k0 + ((j & 1) ? -((j + 1) >> 1) : (j >> 1));   // 0, -1, +1, -2, +2, ...
         k = k < 0 ? k + K : (k >= K ? k - K : k);
