@@ -55,11 +55,12 @@ def parse():
                     help="subset of the workload's distributions (profiling runs)")
     ap.add_argument("--filter-variant", type=int, default=0, choices=[0, 1],
                     help="compaction schedule: 0 two passes, 1 single pass with look-back")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "prior-art", "kgon"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "prior-art", "kgon", "learned"],
                     help="single: the three 1e8 sets; batched: 4096 uneven sets, batched call vs per-set calls; "
                          "prior-art: extremes + filter against the paper's Thrust/CUB variants (context); "
                          "kgon: K-direction filter polygons against the octagon")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
+    ap.add_argument("--train-sets", type=int, default=32, help="training sets per family (learned workload)")
     return ap.parse_args()
 
 
@@ -711,6 +712,95 @@ def run_kgon(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """The learned proposal against the plain octagon, end-to-end hull time
+    on the same GPU.  Training labels come from timings of the plain K-gon
+    path (ch_hull_kgon for every K, without offsets and with random ones)
+    on sets of the proposal's families; the MLP trains with the library's
+    kernels; evaluation on one 10^8-point set per family: the proposal
+    (features + MLP + the K-gon hull, the host reading the 68 outputs)
+    against the plain octagon in the same K-gon pipeline (K = 8, no fan) and
+    against ch_hull (octagon filter + the hull step's fan).  All three hulls
+    must be equal."""
+    import numpy as np
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    import pointgen
+    from paper_2303_10581_gb300 import learned
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n_train, per_family = 1 << 20, args.train_sets
+    prop = learned.Proposal(device=dev, seed=args.seed)
+    t0 = time.perf_counter()
+    ws_small = ch.Workspace(n_train, device=dev)
+    train_sets = [pointgen.make_family(kind, n_train, seed=10_000 * k + s)
+                  for k, kind in enumerate(pointgen.FAMILIES) for s in range(per_family)]
+    X, label, off, mask = learned.make_labels(train_sets, ws_small, prop, seed=args.seed)
+    del ws_small, train_sets
+    hist = prop.train(X, label, off, mask, steps=400, batch=48, lr=3e-3, lam=0.5)
+    train_s = time.perf_counter() - t0
+    counts = np.bincount(label.cpu().numpy(), minlength=4).tolist()
+
+    n = args.n
+    ws = ch.Workspace(n, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    oct_dirs = torch.from_numpy(learned.directions(8)).to(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return round(e0.elapsed_time(e1) / args.steps, 4), round((time.perf_counter() - t1) * 1e3 / args.steps, 4)
+
+    per_family = {}
+    for k, kind in enumerate(pointgen.FAMILIES):
+        d = torch.from_numpy(pointgen.make_family(kind, n, seed=90 + k)).to(dev)
+        ms_fan, _ = timed(lambda: ch.ch_hull(d, out, cnt, ws.buf, stream))
+        h_fan = out[: int(cnt.item())].clone()
+        ms_oct, _ = timed(lambda: ch.ch_hull_kgon(d, oct_dirs, out, cnt, ws.buf, stream))
+        h_oct = out[: int(cnt.item())].clone()
+        res = {}
+
+        def learned_hull():
+            res["h"] = prop.hull(d, ws, stream)
+
+        ms_l, wall_l = timed(learned_hull)
+        idx_l, cnt_l, K = res["h"]
+        h_l = idx_l[: int(cnt_l.item())]
+        ws.check()
+        assert torch.equal(h_fan, h_oct) and torch.equal(h_fan, h_l), kind
+        per_family[kind] = {"learned_ms": ms_l, "learned_wall_ms": wall_l, "learned_K": K,
+                            "octagon_kgon_path_ms": ms_oct, "octagon_with_fan_ms": ms_fan,
+                            "hull_vertices": int(h_fan.numel())}
+        del d
+    mean_l = sum(v["learned_ms"] for v in per_family.values()) / len(per_family)
+    line = {
+        "metric": "end-to-end hull ms: learned K-gon proposal vs the plain octagon (same GPU)",
+        "value": round(mean_l, 4), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f32+exact; MLP bf16 weights, f32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": f"one set of n={n} per family: " + ", ".join(pointgen.FAMILIES),
+                   "training": f"{per_family and len(pointgen.FAMILIES) * args.train_sets} sets of n=2^20, "
+                               f"labels from ch_hull_kgon timings (K in 8,16,32,64; no / 2 random offsets), "
+                               f"400 Adam steps, batch 48",
+                   "label_counts_K8_16_32_64": counts, "final_loss": round(float(np.mean(hist[-20:])), 4),
+                   "train_seconds": round(train_s, 1)},
+        "per_family": per_family,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global DISTS
     args = parse()
@@ -720,6 +810,9 @@ def main():
     if args.workload == "prior-art":
         DISTS = tuple(d for d in args.dists.split(",") if d)
         run_prior_art(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
     if args.workload == "kgon":
         DISTS = tuple(d for d in args.dists.split(",") if d)

@@ -136,6 +136,36 @@ ch_status ch_filter_kgon(const float *pts, int64_t n, const float *dirs, int32_t
 ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *hull_idx,
                        uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- learned proposal of the K-direction polygon (not in the paper: its
+ * extension to more directions, picked per point set) ---------------------
+ * Features of a point set: a 32 x 32 occupancy grid of a sample of
+ * m = min(n, 4096) points (indices floor(j n / m)) over the sample's
+ * bounding box, cell = min(31, floor(fl(fl(x - xmin) * fl(32 / w)))) per
+ * axis (w the box width, 0 scale when w = 0), as fractions of m.  feat:
+ * DEVICE, 1024 floats (row = y cell).  One block; CH_ERR_ARG for n < 1. */
+ch_status ch_kgon_features(const float *pts, int64_t n, float *feat, void *stream);
+
+/* The MLP 1024 -> 64 -> 64 -> 68 (4 logits of K in {8, 16, 32, 64}, 64
+ * angular offsets), ReLU between, BF16 weights, FP32 accumulation.
+ * params: DEVICE bf16[ch_mlp_param_count()], row-major
+ * W1[64][1024] b1[64] W2[64][64] b2[64] W3[68][64] b3[68].  X: DEVICE
+ * float[B][1024]; H1, H2: float[B][64]; OUT: float[B][68] (DEVICE). */
+int32_t ch_mlp_param_count(void);
+ch_status ch_mlp_forward(const float *X, int32_t B, const void *params, float *H1, float *H2, float *OUT,
+                         void *stream);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8, bias-corrected with `step`
+ * >= 1) on the batch: loss = mean over the batch of the softmax
+ * cross-entropy of OUT[0:4] against label[b] (0..3) plus
+ * lam * mask[b] * mean_j (OUT[4+j] - off[b][j])^2.  master, adam_m, adam_v:
+ * DEVICE float[param count] (FP32 master weights and moments); params
+ * receives the BF16 copy of the updated master weights.  scratch: DEVICE
+ * float[ch_mlp_scratch_floats(B)]; loss: DEVICE float[B] (per sample). */
+ch_status ch_mlp_train_step(const float *X, int32_t B, const int32_t *label, const float *off, const float *mask,
+                            float lam, void *params, float *master, float *adam_m, float *adam_v, int32_t step,
+                            float lr, float *scratch, float *loss, void *stream);
+int64_t ch_mlp_scratch_floats(int32_t B);
+
 /* Waits for `stream`, then returns and clears the first device-side error
  * recorded in ws since the last call (CH_OK if none). */
 ch_status ch_last_error(void *ws, void *stream);

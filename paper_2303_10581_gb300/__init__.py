@@ -32,7 +32,8 @@ CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOU
 
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
-           "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon")
+           "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
+           "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
@@ -76,8 +77,16 @@ def load(build_if_missing: bool = True):
     lib.ch_hull_counts.argtypes = [p, sz, i64, p, p]
     lib.ch_filter_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, p, p, sz, p]
     lib.ch_hull_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, sz, p]
+    f32 = ctypes.c_float
+    i32 = ctypes.c_int32
+    lib.ch_kgon_features.argtypes = [p, i64, p, p]
+    lib.ch_mlp_forward.argtypes = [p, i32, p, p, p, p, p]
+    lib.ch_mlp_train_step.argtypes = [p, i32, p, p, p, f32, p, p, p, p, i32, f32, p, p, p]
+    lib.ch_mlp_param_count.argtypes = []
+    lib.ch_mlp_scratch_floats.argtypes = [i32]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
+    lib.ch_mlp_scratch_floats.restype = ctypes.c_int64
     _lib = lib
     return lib
 

@@ -141,3 +141,34 @@ def kgon_offsets(K: int, seed: int, spread: float = 0.45) -> np.ndarray:
     """Random angular offsets in (-spread, spread) * pi / K: the directions
     stay in counter-clockwise order."""
     return (_rng(seed).uniform(-spread, spread, K) * math.pi / K).astype(np.float64)
+
+
+FAMILIES = ("gaussians", "ellipse", "displaced")
+
+
+def make_family(kind: str, n: int, seed: int) -> np.ndarray:
+    """(n, 2) float32 points of one of the learned proposal's training
+    families, randomly scaled and rotated:
+    ``gaussians`` a mixture of 1-4 anisotropic Gaussians; ``ellipse`` points
+    near an ellipse with axis ratio Uniform[1, 20] (radius factor
+    1 - |Normal(0, 0.01)|); ``displaced`` the displaced circle."""
+    rng = _rng(seed)
+    if kind == "gaussians":
+        comps = int(rng.integers(1, 5))
+        which = rng.integers(0, comps, n)
+        means = rng.uniform(-3.0, 3.0, (comps, 2))
+        sig = rng.uniform(0.1, 1.0, (comps, 2))
+        rot = rng.uniform(0.0, 2.0 * math.pi, comps)
+        z = rng.standard_normal((n, 2)) * sig[which]
+        c, s = np.cos(rot[which]), np.sin(rot[which])
+        x = means[which, 0] + c * z[:, 0] - s * z[:, 1]
+        y = means[which, 1] + s * z[:, 0] + c * z[:, 1]
+    else:
+        th = rng.uniform(0.0, 2.0 * math.pi, n)
+        r = 1.0 - np.abs(rng.standard_normal(n)) * 0.01
+        ratio = rng.uniform(1.0, 20.0) if kind == "ellipse" else 1.0
+        u, v = r * np.cos(th), r * np.sin(th) / ratio
+        a = rng.uniform(0.0, 2.0 * math.pi)
+        x, y = math.cos(a) * u - math.sin(a) * v, math.sin(a) * u + math.cos(a) * v
+    scale = rng.uniform(0.1, 10.0)
+    return _pack(x * scale, y * scale)

@@ -18,7 +18,7 @@ def declared_symbols():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names |= set(re.findall(r"\bch_status\s+(ch_\w+)\s*\(", text))
+        names |= set(re.findall(r"\b(?:ch_status|int32_t|int64_t)\s+(ch_\w+)\s*\(", text))
     return names
 
 
