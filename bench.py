@@ -61,6 +61,8 @@ def parse():
                          "kgon: K-direction filter polygons against the octagon")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     ap.add_argument("--train-sets", type=int, default=32, help="training sets per family (learned workload)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched workload: tune the batched call's launch grids first (cached in JSON)")
     return ap.parse_args()
 
 
@@ -519,6 +521,16 @@ def run_batched(args):
         assert h_b[b + 1] - h_b[b] == c1[b], b
         assert np.array_equal(ib[h_b[b]:h_b[b + 1]], i1[offsets[b]:offsets[b] + c1[b]]), b
 
+    tuned = None
+    if args.autotune:
+        from paper_2303_10581_gb300 import autotune
+        tuned = autotune.tune(d_pts, d_off, ws)          # leaves the best grids applied
+        autotune.save(tuned, autotune.cache_key(dev, B, n))
+        batched()
+        torch.cuda.synchronize()
+        ws.check()
+        assert np.array_equal(hoff.cpu().numpy(), h_b) and np.array_equal(idx.cpu().numpy()[: h_b[-1]], ib[: h_b[-1]])
+
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf)
@@ -543,6 +555,7 @@ def run_batched(args):
         "batched_graph_ms": round(ms_graph, 4), "batched_ms": round(ms_batched, 4),
         "per_set_calls_ms": round(ms_loop, 4), "speedup_vs_per_set": round(ms_loop / ms_graph, 2),
         "gpoints_s": round(n / (ms_graph * 1e-3) / 1e9, 3), "gpu_launches_per_batch": int(launches),
+        "autotune": tuned,
     }
     print(json.dumps(line), flush=True)
 

@@ -136,6 +136,22 @@ ch_status ch_filter_kgon(const float *pts, int64_t n, const float *dirs, int32_t
 ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *hull_idx,
                        uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- launch tuning of ch_hull_batched ---------------------------------
+ * Blocks per SM of the batched kernels' grids (results do not depend on
+ * them: every such kernel walks tiles grid-stride or takes them by ticket).
+ * 0 restores the built-in choice.  Process-wide, host-only; CH_ERR_ARG for
+ * an unknown knob or a value outside 0..64.  The Python package's
+ * autotuner sweeps these on a workload and caches the best in JSON. */
+typedef enum {
+    CH_TUNE_BX_EXTREMES = 0,    /* extremes sweep (default 8)                  */
+    CH_TUNE_BX_FILTER = 1,      /* filter count and scatter (default: occupancy) */
+    CH_TUNE_BX_SORT_PASS = 2,   /* radix-sort passes (default: occupancy)      */
+    CH_TUNE_BX_EMIT = 3,        /* chain compaction (default 4)                */
+    CH_TUNE_COUNT = 4
+} ch_tune_knob;
+ch_status ch_tune_set(int32_t knob, int32_t blocks_per_sm);
+ch_status ch_tune_get(int32_t knob, int32_t *blocks_per_sm);
+
 /* ---- learned proposal of the K-direction polygon (not in the paper: its
  * extension to more directions, picked per point set) ---------------------
  * Features of a point set: a 32 x 32 occupancy grid of a sample of

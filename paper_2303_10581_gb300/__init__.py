@@ -33,7 +33,9 @@ CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOU
 SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
            "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
-           "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats")
+           "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
+           "ch_tune_set", "ch_tune_get")
+TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit")
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
@@ -84,6 +86,8 @@ def load(build_if_missing: bool = True):
     lib.ch_mlp_train_step.argtypes = [p, i32, p, p, p, f32, p, p, p, p, i32, f32, p, p, p]
     lib.ch_mlp_param_count.argtypes = []
     lib.ch_mlp_scratch_floats.argtypes = [i32]
+    lib.ch_tune_set.argtypes = [i32, i32]
+    lib.ch_tune_get.argtypes = [i32, ctypes.POINTER(i32)]
     for name in SYMBOLS:
         getattr(lib, name).restype = ctypes.c_int
     lib.ch_mlp_scratch_floats.restype = ctypes.c_int64
@@ -170,6 +174,17 @@ def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):
     _check(load().ch_hull_batched(_ptr(pts, "pts"), _ptr(offsets, "offsets"), offsets.shape[0] - 1,
                                   _ptr(hull_idx, "hull_idx"), _ptr(hull_offsets, "hull_offsets"),
                                   _ptr(ws, "ws"), ws.numel(), _stream(stream)), "ch_hull_batched")
+
+
+def ch_tune_set(knob: str, blocks_per_sm: int):
+    """Blocks per SM of a batched kernel's grid (0: the built-in choice)."""
+    _check(load().ch_tune_set(TUNE_KNOBS.index(knob), int(blocks_per_sm)), "ch_tune_set")
+
+
+def ch_tune_get(knob: str) -> int:
+    v = ctypes.c_int32()
+    _check(load().ch_tune_get(TUNE_KNOBS.index(knob), ctypes.byref(v)), "ch_tune_get")
+    return int(v.value)
 
 
 def ch_hull_counts(ws, n, stream=None):

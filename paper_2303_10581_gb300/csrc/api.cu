@@ -30,6 +30,27 @@ size_t batched_bytes(int64_t n, int64_t B) { return make_batch_layout(make_layou
 
 }  // namespace
 
+namespace ch {
+namespace {
+int g_tune[CH_TUNE_COUNT] = {0, 0, 0, 0};
+}
+int tune_value(int knob) { return knob >= 0 && knob < CH_TUNE_COUNT ? g_tune[knob] : 0; }
+}  // namespace ch
+
+extern "C" ch_status ch_tune_set(int32_t knob, int32_t blocks_per_sm)
+{
+    if (knob < 0 || knob >= CH_TUNE_COUNT || blocks_per_sm < 0 || blocks_per_sm > 64) return CH_ERR_ARG;
+    ch::g_tune[knob] = blocks_per_sm;
+    return CH_OK;
+}
+
+extern "C" ch_status ch_tune_get(int32_t knob, int32_t *blocks_per_sm)
+{
+    if (knob < 0 || knob >= CH_TUNE_COUNT || !blocks_per_sm) return CH_ERR_ARG;
+    *blocks_per_sm = ch::g_tune[knob];
+    return CH_OK;
+}
+
 extern "C" ch_status ch_workspace_size(int64_t n, int64_t num_sets, size_t *bytes)
 {
     if (!bytes || n < 0 || num_sets < 1) return CH_ERR_ARG;

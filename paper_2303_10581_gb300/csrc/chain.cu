@@ -1043,7 +1043,8 @@ cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cu
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int64_t eb = ceil_div(BL.tiles_max, kEmitThreads);
-    if (eb > (int64_t)sms * 4) eb = (int64_t)sms * 4;
+    const int emit_per_sm = tune_value(CH_TUNE_BX_EMIT) ? tune_value(CH_TUNE_BX_EMIT) : 4;
+    if (eb > (int64_t)sms * emit_per_sm) eb = (int64_t)sms * emit_per_sm;
     if (eb < 1) eb = 1;
     probe_before(CH_K_EMIT, st);
     bx_emit_kernel<<<(unsigned)eb, kEmitThreads, 0, st>>>(ws, L, BL);

@@ -416,7 +416,8 @@ __global__ void __launch_bounds__(256) bx_octagon_kernel(const float *__restrict
 
 cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
 {
-    int64_t blocks = std::min<int64_t>(BL.tiles_max, (int64_t)sm_count() * 8);
+    const int per_sm = tune_value(CH_TUNE_BX_EXTREMES) ? tune_value(CH_TUNE_BX_EXTREMES) : 8;
+    int64_t blocks = std::min<int64_t>(BL.tiles_max, (int64_t)sm_count() * per_sm);
     probe_before(CH_K_EXTREMES, st);
     bx_extremes_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(pts, ws, L, BL);
     bx_octagon_kernel<<<(unsigned)ceil_div(BL.num_sets, 8), 256, 0, st>>>(pts, ws, L, BL);

@@ -877,8 +877,9 @@ cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const 
 {
     static int per_sm_c = occupancy(bx_filter_count_kernel, kFiltThreads);
     static int per_sm_s = occupancy(bx_filter_scatter_kernel, kFiltThreads);
-    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_c, BL.tiles_max));
-    const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * per_sm_s, BL.tiles_max));
+    const int tuned = tune_value(CH_TUNE_BX_FILTER);
+    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * (tuned ? tuned : per_sm_c), BL.tiles_max));
+    const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * (tuned ? tuned : per_sm_s), BL.tiles_max));
     probe_before(CH_K_FILTER, st);
     bx_filter_count_kernel<<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, ws, L, BL);
     bx_filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, BL);

@@ -40,6 +40,9 @@ cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, voi
                                   uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count, bool keys_mode,
                                   cudaStream_t st);
 
+// blocks per SM set by ch_tune_set for a batched kernel (0: built-in choice)
+int tune_value(int knob);
+
 // K-direction filter polygon (kfilter.cu): extremes sweep + polygon, then
 // the count pass; returns the count grid through *grid (for the scatter)
 cudaError_t launch_kx_extremes(const float *pts, int64_t n, const float *dirs, int K, uint32_t *ext_out, void *ws,

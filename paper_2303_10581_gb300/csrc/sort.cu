@@ -462,7 +462,9 @@ cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cud
     probe_after(CH_K_SORT_HIST, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t pb = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sm_count() * bx_pass_blocks_per_sm()));
+    const int tuned = tune_value(CH_TUNE_BX_SORT_PASS);
+    const int64_t pb = std::max<int64_t>(
+        1, std::min<int64_t>(cap, (int64_t)sm_count() * (tuned ? tuned : bx_pass_blocks_per_sm())));
     for (int p = 0; p < kSortPasses; ++p) {
         probe_before(CH_K_SORT_PASS, st);
         bx_sort_pass_kernel<<<(unsigned)pb, kSortThreads, sizeof(SortSmem), st>>>(ws, L, BL, p);

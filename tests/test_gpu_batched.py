@@ -185,3 +185,35 @@ def test_cuda_graph_replay():
         for b in range(64):
             want = oracle.convex_hull(p2[offsets[b]:offsets[b + 1]])[2]
             assert np.array_equal(got[h[b]:h[b + 1]], want), (seed, b)
+
+
+@pytest.mark.parametrize("per_sm", [1, 3, 16])
+def test_launch_grids_do_not_change_results(per_sm):
+    """Every batched kernel walks tiles grid-stride or by ticket: any grid
+    gives the same hulls."""
+    pts, offsets, _ = pointgen.make_batch(300, seed=41, min_n=50, max_n=300_000)
+    try:
+        for k in ch.TUNE_KNOBS:
+            ch.ch_tune_set(k, per_sm)
+        check_batch(pts, offsets, sample=range(0, 300, 7))
+    finally:
+        for k in ch.TUNE_KNOBS:
+            ch.ch_tune_set(k, 0)
+
+
+def test_autotuner_keeps_results_and_caches(tmp_path):
+    from paper_2303_10581_gb300 import autotune
+    pts, offsets, _ = pointgen.make_batch(128, seed=43, min_n=100, max_n=100_000)
+    d, o = torch.from_numpy(pts).cuda(), torch.from_numpy(offsets).cuda()
+    ws = ch.Workspace(len(pts), num_sets=128)
+    try:
+        res = autotune.tune(d, o, ws, reps=1)
+        assert res["ms_best"] <= res["ms_default"]
+        assert autotune.current() == res["config"]
+        path = str(tmp_path / "tune.json")
+        key = autotune.cache_key(d.device, 128, len(pts))
+        autotune.save(res, key, path)
+        assert autotune.load_cached(key, path) == res
+        check_batch(pts, offsets, ws, sample=range(0, 128, 5))
+    finally:
+        autotune.apply({})
