@@ -124,6 +124,10 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         self.proc.terminate()
         try:
