@@ -48,6 +48,12 @@
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no long
  * double), so binary32 expressions round exactly once per operation.
+ *
+ * Also the same filter with K directions in place of the eight (the
+ * polygon a learned proposal picks): vertex k maximises the binary32 key
+ * fl(fl(c_k x) + fl(s_k y)), lowest index on ties; the test and the
+ * compaction are those of Sec. 3.2 (oracle_kgon_extremes,
+ * oracle_kgon_filter).
  */
 #include <math.h>
 #include <stdint.h>

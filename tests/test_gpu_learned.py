@@ -89,10 +89,3 @@ def test_learned_hull_is_the_oracle_hull(kind):
     assert ch.ch_last_error(ws.buf) == ch.CH_OK
     assert K in learned.KS
     assert np.array_equal(idx[: int(cnt.item())].cpu().numpy().view(np.uint32), oracle.hull(p))
-
-
-def test_directions_match_the_input_generator():
-    for K in learned.KS:
-        u = np.random.default_rng(K).uniform(-0.4, 0.4, K)
-        assert np.array_equal(learned.directions(K), pointgen.kgon_directions(K))
-        assert np.array_equal(learned.directions(K, u), pointgen.kgon_directions(K, u * np.pi / K))

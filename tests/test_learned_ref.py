@@ -78,3 +78,16 @@ def test_features_constructed_inputs():
 def test_adam_first_step_moves_by_lr():
     w, m, v = mlp.adam(np.zeros(3), np.array([2.0, -3.0, 0.5]), np.zeros(3), np.zeros(3), 1, 0.01)
     assert np.allclose(w, [-0.01, 0.01, -0.01], atol=1e-9)   # bias-corrected: lr * sign(g)
+
+
+def test_proposal_directions_match_the_input_generator():
+    """The directions the learned proposal builds (offsets in units of
+    pi / K) are the input generator's, bit for bit."""
+    import pointgen
+    from paper_2303_10581_gb300 import learned
+    for K in learned.KS:
+        u = np.random.default_rng(K).uniform(-0.4, 0.4, K)
+        assert np.array_equal(learned.directions(K), pointgen.kgon_directions(K))
+        assert np.array_equal(learned.directions(K, u), pointgen.kgon_directions(K, u * np.pi / K))
+    assert np.array_equal(learned.directions(8), np.array(
+        [[1, 0], [1, 1], [0, 1], [-1, 1], [-1, 0], [-1, -1], [0, -1], [1, -1]], np.float32))
