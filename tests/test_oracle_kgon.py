@@ -99,3 +99,17 @@ def test_bad_arguments():
     q[3, 0] = np.nan
     with pytest.raises(oracle.OracleError):
         oracle.kgon_extremes(q, pointgen.kgon_directions(8))
+
+
+def test_hand_worked_polygons():
+    """tests/golden/kgon_hand_worked.json: vertices and survivors worked out
+    by hand (ties, zero-length edges, points on edges and on a chord that is
+    no edge)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "kgon_hand_worked.json")))
+    p = np.array(g["points"], np.float32)
+    for case in g["cases"]:
+        d = np.array(case["dirs"], np.float32)
+        assert oracle.kgon_extremes(p, d).tolist() == case["vertices"], case["name"]
+        assert oracle.kgon_filter(p, d).tolist() == case["survivors"], case["name"]
