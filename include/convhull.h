@@ -76,8 +76,11 @@ ch_status ch_extremes(const float *pts, int64_t n, uint32_t *ext8,
  * compact the kept ones stably.  surv_idx (capacity n) receives the kept
  * indices in ascending order, surv_pts (capacity 2n floats, may be NULL)
  * their coordinates, and *surv_count (device) their number.  ext8 is a
- * device array, normally the output of ch_extremes.  n == 0 writes a zero
- * count. */
+ * device array, normally the output of ch_extremes, but any eight indices
+ * < n are accepted, in any order (repeated, interior or clockwise vertices
+ * included): the result is exact for the vertex sequence given.  An index
+ * >= n sets CH_ERR_ARG in ws and writes a zero count.  n == 0 writes a
+ * zero count. */
 ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8,
                     uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
                     void *ws, size_t ws_bytes, void *stream);
@@ -191,15 +194,19 @@ ch_status ch_last_error(void *ws, void *stream);
  * allocation, or a path under a fixed memory budget or a latency budget
  * that cudaMalloc's implicit synchronisation would break.  The paper has no
  * counterpart; this is a packaging of the same filter.
- * Same arguments, results and error codes as ch_filter, without ws: the
- * scratch lives in a 160 KiB static device array inside the library, held
- * by every GPU that loads it until the process exits.  n is limited to
- * 2^26 = 67,108,864 points (CH_ERR_CAPACITY beyond).  Allocates nothing.
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
- * All calls share the array: calls whose work overlaps on the GPU race and
- * must be serialised by the caller.  Device-side errors cannot be queried
- * (a bad ext8 index yields a zero count). */
+ * Same arguments, results and host-side error codes as ch_filter, without
+ * ws: the scratch lives in a 160 KiB static device array inside the
+ * library, held by every GPU that loads it until the process exits.  n is
+ * limited to 2^26 = 67,108,864 points (CH_ERR_CAPACITY beyond).  Allocates
+ * nothing.  The first call on each device looks up the array's device
+ * address (with that device current) and keeps it; make that first call
+ * before any stream capture.  cudaDeviceReset invalidates the kept address:
+ * do not call this entry point after a reset.  All calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised by the
+ * caller.  Device-side errors (an ext8 index >= n: CH_ERR_ARG; a look-back
+ * wait that gave up: CH_ERR_TIMEOUT) are reported in the count, which then
+ * reads 0x80000000 | code (a valid count is below 2^26); surv_idx and
+ * surv_pts are then unspecified. */
 ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32_t *ext8,
                             uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
                             void *stream);

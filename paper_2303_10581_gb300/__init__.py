@@ -36,6 +36,8 @@ SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter",
            "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
            "ch_tune_set", "ch_tune_get")
 TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit")
+# ch_filter_noalloc reports a device-side error as this bit | the status code in its count
+NOALLOC_FAILED = 0x80000000
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
 
 
@@ -144,7 +146,8 @@ def ch_filter(pts, ext8, surv_idx, surv_pts, surv_count, ws, stream=None):
 def ch_filter_noalloc(pts, ext8, surv_idx, surv_pts, surv_count, stream=None):
     """ch_filter without a workspace, for callers that cannot allocate device
     memory (the library's own static scratch is used; n <= 2^26; calls that
-    overlap on the GPU race)."""
+    overlap on the GPU race).  A device-side error comes back in the count:
+    0x80000000 | code (see NOALLOC_FAILED)."""
     _check(load().ch_filter_noalloc(_ptr(pts, "pts"), pts.shape[0], _ptr(ext8, "ext8"),
                                     _ptr(surv_idx, "surv_idx"), _ptr(surv_pts, "surv_pts"),
                                     _ptr(surv_count, "surv_count"), _stream(stream)), "ch_filter_noalloc")

@@ -69,6 +69,9 @@ struct Octagon {
     uint32_t pad;
     float xl, xh, yl, yh;   // closed quick-discard rectangle (xl > xh: none)
     float cx, cy;           // bounding-box centre, for the edge order
+    float bxl, bxh, byl, byh;   // closed bounding box of the eight vertices
+    uint32_t box_check;     // 1: points may lie outside that box (caller-supplied vertices)
+    uint32_t pad2;
 };
 
 // extremes reduction state: left zeroed by the last block of every sweep

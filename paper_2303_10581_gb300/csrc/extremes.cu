@@ -75,20 +75,44 @@ __device__ __forceinline__ void combine(float &k, uint32_t &i, float ok, uint32_
 // "not left", anything else is decided exactly.  The edge test is disabled
 // (bound = +inf) when the box extents overflow or M > 2^100.
 //
+// The box W x H is the closed bounding box of the eight vertices.  When
+// they are the data's extremes (data_extremes: R, T, L, B really are the
+// largest x, y and smallest x, y of all points) every point lies in it.
+// For vertices chosen by the caller that need not hold, so the record asks
+// the point test to keep every point outside the box first (box_check): a
+// point strictly left of every edge has winding number >= 1 around the
+// vertex sequence, so it lies in the vertices' convex hull and hence in
+// their box; a point outside the box is never strictly inside.  The static
+// bound then holds for every point that reaches the edge test.
+//
 // A closed axis-aligned rectangle whose four corners are, exactly, strictly
 // left of every valid edge lies strictly inside the polygon (the region
 // "strictly left of every edge" is an intersection of open half-planes,
 // hence convex); points in it are discarded with four comparisons.  The
 // largest of a few concentric candidates that passes is kept.
-__device__ void build_octagon_warp(const float2 *pts, const uint32_t *ext8, Octagon *out)
+__device__ void build_octagon_warp(const float2 *pts, const uint32_t *ext8, Octagon *out, bool data_extremes)
 {
     const uint32_t lane = lane_id();
     const uint32_t k = lane & 7u;
     const float2 a = pts[ext8[k]];
     const float2 b = pts[ext8[(k + 1) & 7u]];
-    // bounding box from R, T, L, B
-    const float xmax = pts[ext8[0]].x, ymax = pts[ext8[2]].y;
-    const float xmin = pts[ext8[4]].x, ymin = pts[ext8[6]].y;
+    float xmax, ymax, xmin, ymin;
+    if (data_extremes) {   // bounding box from R, T, L, B
+        xmax = pts[ext8[0]].x;
+        ymax = pts[ext8[2]].y;
+        xmin = pts[ext8[4]].x;
+        ymin = pts[ext8[6]].y;
+    } else {               // bounding box of all eight vertices (lanes k, k ^ 1, ... of each group of 8)
+        xmax = xmin = a.x;
+        ymax = ymin = a.y;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+            xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+            ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+            ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        }
+    }
     const bool valid = !(a.x == b.x && a.y == b.y);
     const float dx = __fsub_rn(b.x, a.x), dy = __fsub_rn(b.y, a.y);
     const float W = __fsub_rn(xmax, xmin), H = __fsub_rn(ymax, ymin);
@@ -146,6 +170,11 @@ __device__ void build_octagon_warp(const float2 *pts, const uint32_t *ext8, Octa
         out->yh = yh;
         out->cx = (float)cxd;
         out->cy = (float)cyd;
+        out->bxl = xmin;
+        out->bxh = xmax;
+        out->byl = ymin;
+        out->byh = ymax;
+        out->box_check = data_extremes ? 0u : 1u;
     }
 }
 
@@ -287,7 +316,7 @@ __global__ void __launch_bounds__(kExtThreads) extremes_kernel(const float *__re
         }
         return;
     }
-    if (build_polygon) build_octagon_warp(reinterpret_cast<const float2 *>(pts), s_ext, oct);
+    if (build_polygon) build_octagon_warp(reinterpret_cast<const float2 *>(pts), s_ext, oct, true);
 }
 
 // Polygon construction for a caller-supplied ext8 (ch_filter); also clears
@@ -314,7 +343,7 @@ __global__ void octagon_kernel(const float *__restrict__ pts, int64_t n, const u
         }
         if (lane < 8) s_ext[lane] = e;
         __syncwarp();
-        build_octagon_warp(reinterpret_cast<const float2 *>(pts), s_ext, oct);
+        build_octagon_warp(reinterpret_cast<const float2 *>(pts), s_ext, oct, false);
     }
 }
 
@@ -411,7 +440,7 @@ __global__ void __launch_bounds__(256) bx_octagon_kernel(const float *__restrict
     }
     if (lane < 8) s_ext[warp][lane] = ~(uint32_t)slots[b * 8 + lane];
     __syncwarp();
-    build_octagon_warp(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, s_ext[warp], out);
+    build_octagon_warp(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, s_ext[warp], out, true);
 }
 
 cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)

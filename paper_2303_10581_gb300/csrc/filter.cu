@@ -41,15 +41,26 @@ namespace ch {
 
 namespace {
 
+// Outside the closed bounding box of the polygon's vertices: never strictly
+// inside the polygon.  Only tested when the vertices were supplied by the
+// caller (BOX); the data's own extremes span a box holding every point.
+template <bool BOX>
+__device__ __forceinline__ bool outside_box(const Octagon &o, float x, float y)
+{
+    if constexpr (BOX) return x < o.bxl || x > o.bxh || y < o.byl || y > o.byh;
+    return false;
+}
+
 // keep(p) <=> NOT (p strictly left of every valid edge); see
-// build_octagon_warp for the error bound of the binary32 test.  The first
-// edge tried is the one facing p's octant around the box centre, which
-// settles points outside the polygon after one test; the order does not
-// change the result.
+// build_octagon_warp for the error bound of the binary32 test, which holds
+// for points inside the vertices' bounding box.  The first edge tried is
+// the one facing p's octant around the box centre, which settles points
+// outside the polygon after one test; the order does not change the result.
+template <bool BOX>
 __device__ __forceinline__ bool keep_point(const Octagon &o, float x, float y)
 {
     if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) return false;
-    if (!o.has_edges) return true;
+    if (!o.has_edges || outside_box<BOX>(o, x, y)) return true;
     const float ux = x - o.cx, uy = y - o.cy;
     int s;
     if (uy >= 0.0f) {
@@ -77,12 +88,13 @@ __device__ __forceinline__ bool keep_point(const Octagon &o, float x, float y)
 constexpr int NW = kFiltThreads / 32;
 
 // A point's first look: 0 discard (inside the quick-discard rectangle), 1
-// keep (proven not strictly left of the edge facing it), 2 deferred (likely
-// strictly inside: every edge must be tested).
+// keep (outside the vertices' box, or proven not strictly left of the edge
+// facing it), 2 deferred (likely strictly inside: every edge must be tested).
+template <bool BOX>
 __device__ __forceinline__ uint32_t first_look(const Octagon &o, float x, float y)
 {
     if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) return 0u;
-    if (!o.has_edges) return 1u;
+    if (!o.has_edges || outside_box<BOX>(o, x, y)) return 1u;
     const float ux = x - o.cx, uy = y - o.cy;
     int e;
     if (uy >= 0.0f) {
@@ -129,7 +141,7 @@ __device__ __forceinline__ void defer(FiltQueue &q, uint32_t item)
 // Tests the queued points (all lanes); returns this lane's keep bits among
 // them and leaves the queue empty.  load(lane, item) reads a point of this
 // warp.
-template <class LoadPoint>
+template <bool BOX, class LoadPoint>
 __device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon &so, bool deferred, LoadPoint load)
 {
     if (!__any_sync(0xffffffffu, deferred)) return 0u;   // the common case: nothing queued
@@ -139,7 +151,7 @@ __device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon
     for (uint32_t i = lane; i < total; i += 32) {
         const uint32_t tg = q.tag[i];
         const float2 v = load(tg >> 4, tg & 15u);
-        if (keep_point(so, v.x, v.y)) atomicOr(&q.res[tg >> 4], 1u << (tg & 15u));
+        if (keep_point<BOX>(so, v.x, v.y)) atomicOr(&q.res[tg >> 4], 1u << (tg & 15u));
     }
     __syncwarp();
     const uint32_t r = q.res[lane];
@@ -163,7 +175,7 @@ __device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout
 // base + (r * 256 + t) * G + h, r < kFiltItems / G, h < G (G = 2: one
 // 16-byte load per row; G = 1: one 8-byte load).  Returns the keep bits
 // (bit r * G + h); positions past n are not kept.
-template <int G>
+template <int G, bool BOX>
 __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int64_t n, int64_t base,
                                               const Octagon &so, float (&px)[kFiltItems], float (&py)[kFiltItems],
                                               FiltQueue &fq)
@@ -198,13 +210,13 @@ __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int
         bool deferred = false;
 #pragma unroll
         for (int q = 0; q < kFiltItems; ++q) {
-            const uint32_t c = first_look(so, px[q], py[q]);
+            const uint32_t c = first_look<BOX>(so, px[q], py[q]);
             if (c == 2u) deferred = true;
             if (c == 1u) keep |= 1u << q;
             else if (c == 2u) defer(fq, (uint32_t)q);
         }
         const uint32_t wbase = tid & ~31u;
-        keep |= resolve_deferred(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+        keep |= resolve_deferred<BOX>(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
             const int64_t i = base + (int64_t)((item / G) * kFiltThreads + wbase + ln) * G + item % G;
             return reinterpret_cast<const float2 *>(pts)[i];
         });
@@ -221,7 +233,7 @@ __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int
                     const float2 v = p2[i];
                     px[r * G + h] = v.x;
                     py[r * G + h] = v.y;
-                    if (keep_point(so, v.x, v.y)) keep |= 1u << (r * G + h);
+                    if (keep_point<BOX>(so, v.x, v.y)) keep |= 1u << (r * G + h);
                 }
             }
         }
@@ -316,7 +328,7 @@ __device__ __forceinline__ void write_count(bool keys, Ctrl *ctrl, uint32_t *sur
 // ---------------------------------------------------------------------------
 // single pass: ticket-ordered tiles with decoupled look-back
 // ---------------------------------------------------------------------------
-template <int G, bool KEYS>
+template <int G, bool KEYS, bool BOX>
 __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__restrict__ pts, int64_t n,
                                                               void *ws, Layout L, uint32_t *__restrict__ surv_idx,
                                                               float2 *__restrict__ surv_pts,
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
         if (tile >= ntiles) break;
         const int64_t base = tile * kFiltTile;
         float px[kFiltItems], py[kFiltItems];
-        const uint32_t keep = load_test<G>(pts, n, base, so, px, py, s_fq[threadIdx.x >> 5]);
+        const uint32_t keep = load_test<G, BOX>(pts, n, base, so, px, py, s_fq[threadIdx.x >> 5]);
         row_counts<G>(keep, s_off);
         __syncthreads();
         if (warp == 0) {
@@ -378,7 +390,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
 // filt_status[t] receives the survivor count of tile t (low 32 bits); the
 // scan turns it into (offset << 32 | count).  Each thread's 16 keep bits go
 // to keep_bits, so the scatter pass does not test again.
-template <int G>
+template <int G, bool BOX>
 __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float *__restrict__ pts, int64_t n,
                                                                     void *ws, Layout L)
 {
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
             if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
         }
         float px[kFiltItems], py[kFiltItems];
-        const uint32_t keep = load_test<G>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
+        const uint32_t keep = load_test<G, BOX>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
         bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
         uint32_t c = __popc(keep);
 #pragma unroll
@@ -580,14 +592,14 @@ __device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, 
             const float2 v = __ldcs(p2 + i);
             px[r] = v.x;
             py[r] = v.y;
-            const uint32_t c = first_look(so, v.x, v.y);
+            const uint32_t c = first_look<false>(so, v.x, v.y);
             if (c == 2u) deferred = true;
             if (c == 1u) keep |= 1u << r;
             else if (c == 2u) defer(fq, (uint32_t)r);
         }
     }
     const uint32_t wbase = threadIdx.x & ~31u;
-    return keep | resolve_deferred(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+    return keep | resolve_deferred<false>(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
                return p2[lo + (int64_t)item * kFiltThreads + wbase + ln];
            });
 }
@@ -795,10 +807,12 @@ template <int G, bool KEYS>
 cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, cudaStream_t st)
 {
-    static int per_sm = occupancy(filter_kernel<G, KEYS>, kFiltThreads);
+    // the hull step (KEYS) filters with the data's own extremes; ch_filter's
+    // caller-supplied vertices need the bounding-box check
+    static int per_sm = occupancy(filter_kernel<G, KEYS, !KEYS>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, ntiles);
-    filter_kernel<G, KEYS><<<(unsigned)std::max<int64_t>(blocks, 1), kFiltThreads, 0, st>>>(
+    filter_kernel<G, KEYS, !KEYS><<<(unsigned)std::max<int64_t>(blocks, 1), kFiltThreads, 0, st>>>(
         pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
     note_kernels(CH_K_FILTER, 1);
     return cudaGetLastError();
@@ -808,12 +822,12 @@ template <int G, bool KEYS>
 cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                             float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan)
 {
-    static int per_sm_c = occupancy(filter_count_kernel<G>, kFiltThreads);
+    static int per_sm_c = occupancy(filter_count_kernel<G, !KEYS>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
     // both passes use the same grid: block b owns the same tile range
     const int64_t bc = std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
-    filter_count_kernel<G><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    filter_count_kernel<G, !KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
     if (fan) {   // timed as its own group, between the filter's two
         probe_after(CH_K_FILTER, st);
         const cudaError_t e = launch_fan(pts, n, G == 2, bc, ws, L, st);

@@ -15,7 +15,10 @@
 // fault, or on systems where the GPU can reach host memory silently use the
 // wrong memory.  The first call on each device therefore looks up the real
 // device address with cudaGetSymbolAddress (with that device current) and
-// caches it; that first call should be made before any stream capture.
+// caches it; that first call should be made before any stream capture.  A
+// cudaDeviceReset destroys the array with the context, and the cached
+// address with it: after a reset this entry point must not be called again
+// in the same process.
 //
 // All calls share the one array and it keeps whatever the last call left:
 // each call clears the error word with cudaMemsetAsync and the polygon
@@ -23,6 +26,11 @@
 // runs.  Calls whose work overlaps on the GPU (different streams, or
 // several host threads) race on the array and must be serialised by the
 // caller.
+//
+// A caller of this entry point has no workspace to ask ch_last_error about,
+// so device-side errors (a vertex index >= n, a look-back wait that gave
+// up) come back in the count itself: a last one-thread kernel replaces
+// *surv_count by kNoAllocFailed | code when the error word is set.
 #include <mutex>
 
 #include "common.cuh"
@@ -71,6 +79,16 @@ ch_status scratch_address(void **out)
 
 inline bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+constexpr uint32_t kNoAllocFailed = 0x80000000u;   // no valid count reaches 2^31 (n <= 2^26)
+
+// Runs after the filter on the same stream: reports a device-side error of
+// this call through the count.
+__global__ void noalloc_status_kernel(void *scratch, Layout L, uint32_t *surv_count)
+{
+    const uint32_t code = at<Persist>(scratch, L.persist)->error;
+    if (code != 0u) *surv_count = kNoAllocFailed | code;
+}
+
 }  // namespace
 
 }  // namespace ch
@@ -97,7 +115,8 @@ extern "C" ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32
                                    (int64_t)L.zero_words, st);
     if (e != cudaSuccess) return CH_ERR_CUDA;
     // the single-pass schedule: its only scratch is the look-back status
-    return launch_filter(pts, n, scratch, L, surv_idx, surv_pts, surv_count, false, st, 1) == cudaSuccess
-               ? CH_OK
-               : CH_ERR_CUDA;
+    e = launch_filter(pts, n, scratch, L, surv_idx, surv_pts, surv_count, false, st, 1);
+    if (e != cudaSuccess) return CH_ERR_CUDA;
+    noalloc_status_kernel<<<1, 1, 0, st>>>(scratch, L, surv_count);
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ERR_CUDA;
 }

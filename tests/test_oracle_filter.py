@@ -83,3 +83,36 @@ def test_keep_flags_agree_with_filter():
     which = np.arange(len(p), dtype=np.uint32)
     f = oracle.keep_flags(p, e, which)
     assert np.array_equal(np.nonzero(f)[0].astype(np.uint32), s)
+
+
+def _vertex_sequences(p, rng):
+    """Vertex index sequences a caller may hand the filter: the extremes
+    rotated, eight random points, eight points near the centre, R and L
+    swapped, and a sequence with repeats."""
+    e = oracle.extremes(p)
+    c = np.argsort(np.abs(p.astype(np.float64) - np.median(p, 0)).sum(1))[:8]
+    swapped = e.copy()
+    swapped[[0, 4]] = swapped[[4, 0]]
+    return {
+        "rot1": np.roll(e, 1), "rot3": np.roll(e, 3), "rot4": np.roll(e, 4),
+        "random": rng.choice(len(p), 8, replace=False).astype(np.uint32),
+        "interior": c.astype(np.uint32),
+        "swap_RL": swapped,
+        "repeats": np.array([e[0], e[0], e[2], e[2], e[2], e[4], e[6], e[6]], np.uint32),
+    }
+
+
+@pytest.mark.parametrize("dist", pointgen.DISTRIBUTIONS)
+def test_filter_any_vertex_sequence_matches_exact_definition(dist):
+    """The filter's definition holds for any eight vertices, not only for
+    the extremes: discarded <=> strictly left of every edge of non-zero
+    length (rationals), whatever the order or position of the vertices."""
+    rng = np.random.default_rng(23)
+    p = pointgen.make_points(dist, 700, seed=24)
+    for name, ext in _vertex_sequences(p, rng).items():
+        s = oracle.filter_points(p, ext)
+        poly = [p[i] for i in ext]
+        kept = np.zeros(len(p), bool)
+        kept[s] = True
+        for i in range(len(p)):
+            assert kept[i] == (not strictly_inside_q(poly, p[i])), (name, i)
