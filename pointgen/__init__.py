@@ -18,6 +18,8 @@ All draws are binary64 and rounded once to binary32; points are packed
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -59,12 +61,55 @@ def make_points(dist: str, n: int, seed: int, chunk: int = 1 << 24) -> np.ndarra
     return out
 
 
-def make_batch(num_sets: int, seed: int, min_n: int = 100, max_n: int = 1_000_000):
+def _fill_blocks(fn, nblocks: int, workers: int | None):
+    """fn(b) for b < nblocks, on `workers` threads (numpy's generators and
+    ufuncs release the GIL); each block draws from its own generator, so
+    the result does not depend on the thread count."""
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1:
+        for b in range(nblocks):
+            fn(b)
+        return
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(fn, range(nblocks)))
+
+
+def make_points_blocked(dist: str, n: int, seed: int, block: int = 1 << 24, workers: int | None = None) -> np.ndarray:
+    """(n, 2) float32 points of one distribution, like make_points, but block
+    k of `block` points draws from its own stream (SeedSequence(seed)
+    spawned once per block), so large sets are generated on several threads
+    and the result still depends only on (dist, n, seed, block)."""
+    if dist not in DISTRIBUTIONS:
+        raise ValueError(f"unknown distribution {dist!r}")
+    nblocks = (n + block - 1) // block
+    seqs = np.random.SeedSequence(seed).spawn(max(nblocks, 1))
+    out = np.empty((n, 2), dtype=np.float32)
+
+    def fill(b):
+        lo = b * block
+        m = min(block, n - lo)
+        rng = np.random.Generator(np.random.PCG64(seqs[b]))
+        if dist == "normal":
+            out[lo:lo + m, 0] = rng.standard_normal(m)
+            out[lo:lo + m, 1] = rng.standard_normal(m)
+        else:
+            theta = rng.uniform(0.0, 2.0 * math.pi, m)
+            r = 1.0 if dist == "circle" else 1.0 - np.abs(rng.normal(0.0, 0.01, m))
+            out[lo:lo + m, 0] = r * np.cos(theta)
+            out[lo:lo + m, 1] = r * np.sin(theta)
+
+    _fill_blocks(fill, nblocks, workers)
+    return out
+
+
+def make_batch(num_sets: int, seed: int, min_n: int = 100, max_n: int = 1_000_000, workers: int | None = None):
     """Independent sets of uneven sizes, concatenated in CSR form.
 
     Sizes are log-uniform in [min_n, max_n]; each set draws its distribution
     uniformly from the three above, is scaled by Uniform[0.1, 10] and rotated
-    by Uniform[0, 2 pi) (in binary64, then rounded to binary32).
+    by Uniform[0, 2 pi) (in binary64, then rounded to binary32).  Every set
+    has its own generator (seeded from the batch's), so the sets are filled
+    on `workers` threads with the same result.
     Returns (points (N, 2) float32, offsets (num_sets + 1,) int64, dists list).
     """
     rng = _rng(seed)
@@ -76,10 +121,10 @@ def make_batch(num_sets: int, seed: int, min_n: int = 100, max_n: int = 1_000_00
     offsets = np.zeros(num_sets + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
     pts = np.empty((int(offsets[-1]), 2), dtype=np.float32)
-    dists = []
-    for b in range(num_sets):
-        dist = DISTRIBUTIONS[int(kinds[b])]
-        dists.append(dist)
+    dists = [DISTRIBUTIONS[int(k)] for k in kinds]
+
+    def fill(b):
+        dist = dists[b]
         r2 = _rng(int(sub_seeds[b]))
         m = int(sizes[b])
         if dist == "normal":
@@ -94,6 +139,8 @@ def make_batch(num_sets: int, seed: int, min_n: int = 100, max_n: int = 1_000_00
         sc = scales[b]
         pts[offsets[b]:offsets[b + 1], 0] = sc * (c * x - s * y)
         pts[offsets[b]:offsets[b + 1], 1] = sc * (s * x + c * y)
+
+    _fill_blocks(fill, num_sets, workers)
     return pts, offsets, dists
 
 
