@@ -61,6 +61,8 @@ def parse():
                          "kgon: K-direction filter polygons against the octagon")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     ap.add_argument("--train-sets", type=int, default=32, help="training sets per family (learned workload)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the records of the 10^9-point filter, the batch and the learned proposal")
     ap.add_argument("--autotune", action="store_true",
                     help="batched workload: tune the batched call's launch grids first (cached in JSON)")
     return ap.parse_args()
@@ -226,9 +228,15 @@ def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev):
     peak = sms * 4 * mhz * 1e6 / 1e12                          # T warp-instructions/s
     achieved = inst / (dom_ms * 1e-3) / 1e12
     per_launch_bytes = algorithmic_bytes("kgon", n, s_list, t_list) * steps / dom_launches
+    hbm_peak, hbm_kind = peaks()
+    hbm_gbs = per_launch_bytes / (dom_ms / dom_launches * 1e-3) / 1e9
     return {"kernel": "kgon", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "T warp-instr/s", "frac": round(achieved / peak, 4),
             "peak_source": f"derived: {sms} SMs x 4 issue slots x {mhz:.0f} MHz",
+            # the same launches against the HBM roofline: algorithmic bytes
+            # (8 B per octagon survivor tested) over the event time
+            "hbm_achieved_gbs": round(hbm_gbs, 1), "hbm_peak_gbs": hbm_peak,
+            "hbm_frac": round(hbm_gbs / hbm_peak, 4), "hbm_peak_source": hbm_kind,
             "traffic": int(tr["dram_per_algorithmic_byte"] * per_launch_bytes),
             "traffic_source": tr["capture"], "algorithmic_bytes_per_launch": int(per_launch_bytes),
             "warp_instr_per_launch": int(inst / dom_launches), "avg_launch_ms": round(dom_ms / dom_launches, 4)}
@@ -447,6 +455,14 @@ def run_ours(args):
         cpu = {"value": round(rate, 5), "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample_n} points of each distribution (3 sets), whole path, {dt:.1f} s"}
 
+    # the other configurations of the metric, one record each (one GPU only;
+    # outside the timed region above)
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["filter_1e9"] = filter_1e9_record(dev, stream, max(5, args.steps), args.warmup, peak, peak_kind)
+        extra["batched"] = batched_record(dev, stream, max(5, args.steps), args.warmup)
+        extra["learned_vs_octagon"] = learned_record(dev, stream, n, 3, 2, args.train_sets, args.seed)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "Gpoints/s", "n_gpus": world, "steps": args.steps,
@@ -461,6 +477,7 @@ def run_ours(args):
             "hull_ms_per_set": {d: round(sum(v.values()), 4) for d, v in per_set.items()},
             "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu,
+            **extra,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -469,6 +486,131 @@ def run_ours(args):
 
 BATCH_WORKLOAD = ("{B} independent sets, sizes log-uniform in [1e2, 1e6] points, distribution drawn from "
                   "normal / circle / displaced circle, scaled by U[0.1, 10], rotated by U[0, 2 pi)")
+
+# --------------------------------------------------------------------------- the other configurations
+
+N_1E9 = 1_000_000_000
+
+
+def ev_time(fn, steps, warmup, stream):
+    """Average ms of one call of fn: CUDA events on `stream` around `steps`
+    calls, after `warmup` untimed calls, synchronised on both sides."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
+def _rate(bytes_, ms, peak):
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return round(gbs, 1), round(gbs / peak, 4)
+
+
+def filter_1e9_record(dev, stream, steps, warmup, peak, peak_kind):
+    """The 10^9-point configuration (8 GB of packed float2, Normal(0,1),
+    seed 1 -- the set the large parity test compares with the oracle):
+    ch_extremes, then ch_filter with each compaction schedule, then
+    ch_hull, each timed alone with CUDA events over `steps` calls (the
+    input is larger than L2).  GB/s from algorithmic bytes: 8 B per point
+    read, 12 B per survivor written (index + point)."""
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    import pointgen
+
+    n = N_1E9
+    host = pointgen.make_points_blocked("normal", n, seed=1)
+    d = torch.from_numpy(host).to(dev)
+    del host
+    ws = ch.Workspace(n, device=dev)
+    ext = torch.zeros(8, dtype=torch.int32, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    sp = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    rec = {"workload": "single set, n=1e9 fp32 Normal(0,1), seed 1 (8 GB packed float2, larger than L2)",
+           "peak_gbs": peak, "peak_source": peak_kind, "steps": steps, "warmup": warmup}
+    e_ms = ev_time(lambda: ch.ch_extremes(d, ext, ws.buf, stream), steps, warmup, stream)
+    gbs, frac = _rate(8 * n, e_ms, peak)
+    rec["extremes"] = {"ms": round(e_ms, 4), "gbs": gbs, "frac_of_peak": frac}
+    for variant, name in ((0, "two_pass"), (1, "single_pass")):
+        ch.ch_filter_variant(variant)
+        try:
+            f_ms = ev_time(lambda: ch.ch_filter(d, ext, idx, sp, cnt, ws.buf, stream), steps, warmup, stream)
+        finally:
+            ch.ch_filter_variant(0)
+        ws.check()
+        s = int(cnt.item())
+        gbs, frac = _rate(8 * n + 12 * s, f_ms, peak)
+        rec[name] = {"ms": round(f_ms, 4), "gpoints_s": round(n / (f_ms * 1e-3) / 1e9, 1), "gbs": gbs,
+                     "frac_of_peak": frac, "survivors": s}
+    h_ms = ev_time(lambda: ch.ch_hull(d, idx, cnt, ws.buf, stream), steps, warmup, stream)
+    ws.check()
+    rec["hull"] = {"ms": round(h_ms, 4), "gpoints_s": round(n / (h_ms * 1e-3) / 1e9, 1),
+                   "hull_vertices": int(cnt.item())}
+    rec["target_0.7_met"] = rec["two_pass"]["frac_of_peak"] >= 0.7
+    del d, ws, idx, sp
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec
+
+
+def batched_record(dev, stream, steps, warmup, B=4096, seed=1):
+    """The batched configuration: one ch_hull_batched call over B uneven
+    sets, captured in a CUDA graph, graph replays timed with CUDA events
+    (inputs 3.6 GB, larger than L2).  Launch grids: the autotuner's cached
+    choice for this GPU and batch shape when there is one, else the
+    built-in ones."""
+    import torch
+
+    import paper_2303_10581_gb300 as ch
+    import pointgen
+    from paper_2303_10581_gb300 import autotune
+
+    pts, offsets, _ = pointgen.make_batch(B, seed=seed)
+    n = len(pts)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_off = torch.from_numpy(offsets).to(dev)
+    del pts
+    ws = ch.Workspace(n, num_sets=B, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    hoff = torch.zeros(B + 1, dtype=torch.int64, device=dev)
+    saved = autotune.current()
+    cached = autotune.load_cached(autotune.cache_key(dev, B, n))
+    if cached:
+        autotune.apply(cached)
+    try:
+        ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf, stream)
+        torch.cuda.synchronize()
+        ws.check()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf)
+        ms = ev_time(graph.replay, steps, warmup, stream)
+        ws.check()
+        ch.ch_probe_start(ch.KERNELS, max_launches=64)
+        ch.ch_hull_batched(d_pts, d_off, idx, hoff, ws.buf, stream)
+        launches = sum(v[1] for v in ch.ch_probe_stop().values())
+        ws.check()
+    finally:
+        autotune.apply(saved)
+    rec = {"workload": BATCH_WORKLOAD.format(B=B) + f", seed {seed}", "points": int(n), "sets": B,
+           "graph_replay_ms": round(ms, 4), "gpoints_s": round(n / (ms * 1e-3) / 1e9, 2),
+           "hull_vertices": int(hoff[-1].item()), "gpu_launches_per_batch": int(launches),
+           "launch_grids": "autotuned (cached)" if cached else "built-in"}
+    del graph, d_pts, d_off, ws, idx
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec
+
+
 
 
 def run_batched(args):
@@ -736,12 +878,12 @@ def run_kgon(args):
     print(json.dumps(line), flush=True)
 
 
-def run_learned(args):
+def learned_record(dev, stream, n, steps, warmup, train_sets, seed):
     """The learned proposal against the plain octagon, end-to-end hull time
     on the same GPU.  Training labels come from timings of the plain K-gon
     path (ch_hull_kgon for every K, without offsets and with random ones)
     on sets of the proposal's families; the MLP trains with the library's
-    kernels; evaluation on one 10^8-point set per family: the proposal
+    kernels; evaluation on one n-point set per family: the proposal
     (features + MLP + the K-gon hull, the host reading the 68 outputs)
     against the plain octagon in the same K-gon pipeline (K = 8, no fan) and
     against ch_hull (octagon filter + the hull step's fan).  All three hulls
@@ -753,39 +895,35 @@ def run_learned(args):
     import pointgen
     from paper_2303_10581_gb300 import learned
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream(dev)
-    n_train, per_family = 1 << 20, args.train_sets
-    prop = learned.Proposal(device=dev, seed=args.seed)
+    n_train, per_family = 1 << 20, train_sets
+    prop = learned.Proposal(device=dev, seed=seed)
     t0 = time.perf_counter()
     ws_small = ch.Workspace(n_train, device=dev)
-    train_sets = [pointgen.make_family(kind, n_train, seed=10_000 * k + s)
-                  for k, kind in enumerate(pointgen.FAMILIES) for s in range(per_family)]
-    X, label, off, mask = learned.make_labels(train_sets, ws_small, prop, seed=args.seed)
-    del ws_small, train_sets
+    sets = [pointgen.make_family(kind, n_train, seed=10_000 * k + s)
+            for k, kind in enumerate(pointgen.FAMILIES) for s in range(per_family)]
+    X, label, off, mask = learned.make_labels(sets, ws_small, prop, seed=seed)
+    del ws_small, sets
     hist = prop.train(X, label, off, mask, steps=400, batch=48, lr=3e-3, lam=0.5)
     train_s = time.perf_counter() - t0
     counts = np.bincount(label.cpu().numpy(), minlength=4).tolist()
 
-    n = args.n
     ws = ch.Workspace(n, device=dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     oct_dirs = torch.from_numpy(learned.directions(8)).to(dev)
 
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return round(e0.elapsed_time(e1) / args.steps, 4), round((time.perf_counter() - t1) * 1e3 / args.steps, 4)
+        return round(e0.elapsed_time(e1) / steps, 4), round((time.perf_counter() - t1) * 1e3 / steps, 4)
 
     per_family = {}
     for k, kind in enumerate(pointgen.FAMILIES):
@@ -808,19 +946,37 @@ def run_learned(args):
                             "octagon_kgon_path_ms": ms_oct, "octagon_with_fan_ms": ms_fan,
                             "hull_vertices": int(h_fan.numel())}
         del d
+    del ws, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     mean_l = sum(v["learned_ms"] for v in per_family.values()) / len(per_family)
+    return {
+        "workload": f"one set of n={n} per family: " + ", ".join(pointgen.FAMILIES),
+        "training": f"{len(pointgen.FAMILIES) * train_sets} sets of n=2^20, labels from ch_hull_kgon timings "
+                    f"(K in 8,16,32,64; no / 2 random offsets), 400 Adam steps, batch 48",
+        "label_counts_K8_16_32_64": counts, "final_loss": round(float(np.mean(hist[-20:])), 4),
+        "train_seconds": round(train_s, 1), "learned_ms_mean": round(mean_l, 4),
+        "octagon_with_fan_ms_mean": round(sum(v["octagon_with_fan_ms"] for v in per_family.values())
+                                          / len(per_family), 4),
+        "per_family": per_family,
+    }
+
+
+def run_learned(args):
+    """The learned workload alone (one JSON line); see learned_record."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rec = learned_record(dev, stream, args.n, args.steps, args.warmup, args.train_sets, args.seed)
     line = {
         "metric": "end-to-end hull ms: learned K-gon proposal vs the plain octagon (same GPU)",
-        "value": round(mean_l, 4), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "value": rec["learned_ms_mean"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "dtype": "f32+exact; MLP bf16 weights, f32 accumulate",
         "data": "synthetic",
-        "config": {"workload": f"one set of n={n} per family: " + ", ".join(pointgen.FAMILIES),
-                   "training": f"{per_family and len(pointgen.FAMILIES) * args.train_sets} sets of n=2^20, "
-                               f"labels from ch_hull_kgon timings (K in 8,16,32,64; no / 2 random offsets), "
-                               f"400 Adam steps, batch 48",
-                   "label_counts_K8_16_32_64": counts, "final_loss": round(float(np.mean(hist[-20:])), 4),
-                   "train_seconds": round(train_s, 1)},
-        "per_family": per_family,
+        "config": {k: rec[k] for k in ("workload", "training", "label_counts_K8_16_32_64", "final_loss",
+                                       "train_seconds")},
+        "per_family": rec["per_family"],
     }
     print(json.dumps(line), flush=True)
 

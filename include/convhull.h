@@ -26,6 +26,19 @@
  *    is enqueued then.  Errors found on the device (non-finite input, a
  *    look-back wait that timed out) are recorded in `ws` and reported by
  *    ch_last_error(); outputs of a failed call are unspecified.
+ *  - Host threads: apart from thread-safe caches of device properties, the
+ *    compute entry points keep no host state between calls, so several
+ *    host threads may drive them at once, each on its own stream and
+ *    workspace.  Three settings are process-wide instead:
+ *    the compaction schedule (ch_filter_variant), the batched launch grids
+ *    (ch_tune_set) and the instrumentation (ch_probe_start/stop).  The two
+ *    settings are atomics read when a call enqueues its kernels, so a call
+ *    running concurrently with a change uses either the old or the new
+ *    value (results are the same either way, only the schedule differs);
+ *    set them before the calls they are meant for.  The probe's event
+ *    lists are meant for one host thread at a time: while a probe is
+ *    active, make the calls it should time from the thread that started
+ *    it, and no calls from others.
  *  - Point indices are uint32: n < 2^32 (ch_hull: n < 2^30).
  *  - Orientation signs are exact (binary32 fast test with a proven error
  *    bound, then binary64, then error-free expansion arithmetic).
@@ -142,7 +155,8 @@ ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K
 /* ---- launch tuning of ch_hull_batched ---------------------------------
  * Blocks per SM of the batched kernels' grids (results do not depend on
  * them: every such kernel walks tiles grid-stride or takes them by ticket).
- * 0 restores the built-in choice.  Process-wide, host-only; CH_ERR_ARG for
+ * 0 restores the built-in choice.  Process-wide (see "Host threads"
+ * above), host-only; CH_ERR_ARG for
  * an unknown knob or a value outside 0..64.  The Python package's
  * autotuner sweeps these on a workload and caches the best in JSON. */
 typedef enum {
@@ -217,7 +231,7 @@ ch_status ch_filter_noalloc(const float *pts, int64_t n, const uint32_t *ext8,
  * of every 4096-point tile, a scan of the counts, and a scatter pass that
  * revisits only tiles with survivors.  1: one pass -- tiles in ticket order
  * with a decoupled look-back for their output offsets.  CH_ERR_ARG for any
- * other value.  Host-only. */
+ * other value.  Host-only; process-wide (see "Host threads" above). */
 ch_status ch_filter_variant(int32_t variant);
 
 /* ---- instrumentation (not part of the paper's method) ------------------
@@ -246,7 +260,8 @@ typedef enum {
  * two for CHAIN (chains, tree merge); four for KGON (bins, fan vertices,
  * estimate, refine of the keep decisions).  Kernel-launch
  * counting for all ids restarts at zero.  Host-only bookkeeping; creates
- * the events. */
+ * the events.  Process-wide: one probe at a time, driven from one host
+ * thread (see "Host threads" above). */
 ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
 
 /* After a ch_hull call for n points on ws has completed (waits for

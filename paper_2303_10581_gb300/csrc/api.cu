@@ -3,6 +3,7 @@
 // allocation, no host synchronisation (except ch_last_error), no host
 // fallback: every step of Algorithm 1 runs in the kernels of this library.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "common.cuh"
@@ -32,22 +33,26 @@ size_t batched_bytes(int64_t n, int64_t B) { return make_batch_layout(make_layou
 
 namespace ch {
 namespace {
-int g_tune[CH_TUNE_COUNT] = {0, 0, 0, 0};
+// process-wide knobs, read when a batched call enqueues its kernels
+std::atomic<int> g_tune[CH_TUNE_COUNT] = {};
 }
-int tune_value(int knob) { return knob >= 0 && knob < CH_TUNE_COUNT ? g_tune[knob] : 0; }
+int tune_value(int knob)
+{
+    return knob >= 0 && knob < CH_TUNE_COUNT ? g_tune[knob].load(std::memory_order_relaxed) : 0;
+}
 }  // namespace ch
 
 extern "C" ch_status ch_tune_set(int32_t knob, int32_t blocks_per_sm)
 {
     if (knob < 0 || knob >= CH_TUNE_COUNT || blocks_per_sm < 0 || blocks_per_sm > 64) return CH_ERR_ARG;
-    ch::g_tune[knob] = blocks_per_sm;
+    ch::g_tune[knob].store(blocks_per_sm, std::memory_order_relaxed);
     return CH_OK;
 }
 
 extern "C" ch_status ch_tune_get(int32_t knob, int32_t *blocks_per_sm)
 {
     if (knob < 0 || knob >= CH_TUNE_COUNT || !blocks_per_sm) return CH_ERR_ARG;
-    *blocks_per_sm = ch::g_tune[knob];
+    *blocks_per_sm = ch::g_tune[knob].load(std::memory_order_relaxed);
     return CH_OK;
 }
 

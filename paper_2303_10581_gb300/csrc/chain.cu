@@ -987,13 +987,12 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
 {
     const int sms = sm_count();
     int64_t cb = L.n_chunks;
-    static int per_sm = 0;
-    if (!per_sm) {
+    static const int per_sm = [] {   // thread-safe one-time initialisation
         cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChainSmem));
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, chain_kernel, LT, sizeof(ChainSmem));
-        per_sm = v > 0 ? v : 1;
-    }
+        return v > 0 ? v : 1;
+    }();
     if (cb > (int64_t)sms * per_sm) cb = (int64_t)sms * per_sm;
     if (cb < 1) cb = 1;
     probe_before(CH_K_CHAIN, st);
@@ -1025,13 +1024,12 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
 cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
 {
     const int sms = sm_count();
-    static int per_sm = 0;
-    if (!per_sm) {
+    static const int per_sm = [] {   // thread-safe one-time initialisation
         cudaFuncSetAttribute(bx_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ChainSmem));
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, bx_chain_kernel, LT, sizeof(ChainSmem));
-        per_sm = v > 0 ? v : 1;
-    }
+        return v > 0 ? v : 1;
+    }();
     int64_t cb = BL.tiles_max;
     if (cb > (int64_t)sms * per_sm) cb = (int64_t)sms * per_sm;
     if (cb < 1) cb = 1;

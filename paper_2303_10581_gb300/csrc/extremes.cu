@@ -14,6 +14,7 @@
 // which selects the largest key and, among equal keys, the lowest index.
 // The last block to finish decodes the winners and builds the polygon.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "launch.h"
@@ -457,16 +458,18 @@ cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, cons
 
 int sm_count()
 {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64] = {};   // per device; several host threads may fill it
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = v > 0 ? v : 1;
+        c = v > 0 ? v : 1;
+        cached[dev].store(c, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return c;
 }
 
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,

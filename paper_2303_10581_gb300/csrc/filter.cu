@@ -33,6 +33,7 @@
 // Memory traffic: 8 bytes per point read (twice for tiles with survivors in
 // the two-pass variant), 12 bytes per kept point written.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "launch.h"
@@ -840,7 +841,10 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     return cudaGetLastError();
 }
 
-int g_filter_variant = 0;   // 0: two passes, 1: single pass with look-back
+// 0: two passes, 1: single pass with look-back; process-wide, read once per
+// call when its kernels are enqueued (an atomic, so setting it from another
+// host thread is not a data race)
+std::atomic<int> g_filter_variant{0};
 
 template <int G, bool KEYS>
 cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
@@ -860,7 +864,7 @@ cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant,
                           bool fan)
 {
-    const int v = variant < 0 ? g_filter_variant : variant;
+    const int v = variant < 0 ? g_filter_variant.load(std::memory_order_relaxed) : variant;
     const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
     if (keys_mode)
         return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan)
@@ -908,6 +912,6 @@ cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const 
 extern "C" ch_status ch_filter_variant(int32_t variant)
 {
     if (variant != 0 && variant != 1) return CH_ERR_ARG;
-    ch::g_filter_variant = variant;
+    ch::g_filter_variant.store(variant, std::memory_order_relaxed);
     return CH_OK;
 }

@@ -427,26 +427,24 @@ __global__ void __launch_bounds__(kSortThreads, 3) bx_sort_pass_kernel(void *ws,
 
 int pass_blocks_per_sm()
 {
-    static int cached = 0;
-    if (!cached) {
+    static const int cached = [] {   // thread-safe one-time initialisation
         cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sort_pass_kernel, kSortThreads, sizeof(SortSmem));
-        cached = v > 0 ? v : 1;
-    }
+        return v > 0 ? v : 1;
+    }();
     return cached;
 }
 
 int bx_pass_blocks_per_sm()
 {
-    static int cached = 0;
-    if (!cached) {
+    static const int cached = [] {
         cudaFuncSetAttribute(bx_sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SortSmem));
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, bx_sort_pass_kernel, kSortThreads, sizeof(SortSmem));
-        cached = v > 0 ? v : 1;
-    }
+        return v > 0 ? v : 1;
+    }();
     return cached;
 }
 
