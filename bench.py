@@ -328,7 +328,7 @@ def run_ours(args):
     # one probed step, set by set: event time of every kernel
     per_set = {}
     probe_all = {k: (0.0, 0) for k in KERNEL_IDS}
-    surv, sorted_pts = [], []
+    surv, sorted_pts, spec = [], [], []
     for k in range(len(DISTS)):
         ch.ch_probe_start(KERNEL_IDS, max_launches=64)
         ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
@@ -338,6 +338,7 @@ def run_ours(args):
         c = ch.ch_hull_counts(ws.buf, n, stream)
         surv.append(c[0])
         sorted_pts.append(c[1])
+        spec.append(c[2])
     ws.check()
     dominant = max(probe_all, key=lambda k: probe_all[k][0])
     total_probe = sum(v[0] for v in probe_all.values())
@@ -471,6 +472,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n_per_set": n, "sets_per_step": len(DISTS),
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
                        "survivors": dict(zip(DISTS, surv)), "sorted": dict(zip(DISTS, sorted_pts)),
+                       "speculative_sweep": dict(zip(DISTS, spec)),
                        "hull_sizes": dict(zip(DISTS, hull_sizes))},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roof, "filter": filt, "kernel_shares": shares, "kernel_ms_per_set": per_set,

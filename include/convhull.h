@@ -98,6 +98,23 @@ ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8,
                     uint32_t *surv_idx, float *surv_pts, uint32_t *surv_count,
                     void *ws, size_t ws_bytes, void *stream);
 
+/* Sec. 3.1 + Sec. 3.2 in one call (Algorithm 1, steps 1-3): ext8 (device,
+ * 8 entries) receives the eight vertices exactly as ch_extremes gives
+ * them, and surv_idx / surv_pts / *surv_count the survivors of the filter
+ * with that polygon exactly as ch_filter gives them.  On sets of at least
+ * 2^22 points with the two-pass schedule (ch_filter_variant 0) it runs the
+ * speculative single sweep: a first kernel builds an octagon P0 from a
+ * 65,536-point sample; the extremes sweep also writes, as candidates, the
+ * points it cannot prove strictly inside P0; when its last block proves
+ * P0 inside the final octagon (exact signs) and no candidate segment
+ * overflowed, only the candidates are tested and written, so the points
+ * are read once.  Otherwise the filter's two passes run over all points.
+ * The results are the same either way.  Errors as ch_extremes and
+ * ch_filter; n == 0 writes a zero count. */
+ch_status ch_extremes_filter(const float *pts, int64_t n, uint32_t *ext8, uint32_t *surv_idx,
+                             float *surv_pts, uint32_t *surv_count, void *ws, size_t ws_bytes,
+                             void *stream);
+
 /* Algorithm 1 end to end on the device: extremes, filter, then Andrew's
  * monotone chain over the survivors (Sec. 3.3; the paper hands this step to
  * a CPU library, here it stays on the GPU).  hull_idx (capacity n)
@@ -267,7 +284,10 @@ ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
 /* After a ch_hull call for n points on ws has completed (waits for
  * `stream`): counts[0] = points that survived the octagon filter,
  * counts[1] = points the hull step sorted (fewer when its fan of triangles
- * around the bounding-box centre removed some).
+ * around the bounding-box centre removed some), counts[2] = 1 when the
+ * speculative single sweep served the filter (the extremes sweep proved
+ * every point but its candidates strictly inside the octagon, so the
+ * filter read only the candidates), else 0.  counts holds 3 entries.
  * Instrumentation; CH_ERR_ARG / CH_ERR_CAPACITY as for ch_hull. */
 ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32_t *counts, void *stream);
 

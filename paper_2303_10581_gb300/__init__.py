@@ -7,7 +7,7 @@ runs in the CUDA kernels of ``_lib/libconvhull.so``.  There is no CPU
 fallback: if the library cannot be loaded, or a tensor is not on a CUDA
 device, the call raises.
 
-Low-level names mirror the C ABI (``ch_extremes``, ``ch_filter``,
+Low-level names mirror the C ABI (``ch_extremes``, ``ch_filter``, ``ch_extremes_filter``,
 ``ch_hull``, ``ch_hull_batched``, ``ch_workspace_size``,
 ``ch_workspace_init``, ``ch_last_error``); ``Workspace``, ``extremes``,
 ``filter_points`` and ``convex_hull`` are conveniences built on them.
@@ -30,7 +30,7 @@ STATUS = {
 }
 CH_OK, CH_ERR_ARG, CH_ERR_NONFINITE, CH_ERR_CAPACITY, CH_ERR_CUDA, CH_ERR_TIMEOUT, CH_ERR_UNSUPPORTED = range(7)
 
-SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_hull",
+SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter", "ch_extremes_filter", "ch_hull",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
            "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
            "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True):
     lib.ch_workspace_init.argtypes = [p, sz, p]
     lib.ch_extremes.argtypes = [p, i64, p, p, sz, p]
     lib.ch_filter.argtypes = [p, i64, p, p, p, p, p, sz, p]
+    lib.ch_extremes_filter.argtypes = [p, i64, p, p, p, p, p, sz, p]
     lib.ch_hull.argtypes = [p, i64, p, p, p, sz, p]
     lib.ch_hull_batched.argtypes = [p, p, ctypes.c_int32, p, p, p, sz, p]
     lib.ch_last_error.argtypes = [p, p]
@@ -143,6 +144,14 @@ def ch_filter(pts, ext8, surv_idx, surv_pts, surv_count, ws, stream=None):
                             ws.numel(), _stream(stream)), "ch_filter")
 
 
+def ch_extremes_filter(pts, ext8, surv_idx, surv_pts, surv_count, ws, stream=None):
+    """ch_extremes + ch_filter in one call (the speculative single sweep on
+    large sets); ext8 is an output here."""
+    _check(load().ch_extremes_filter(_ptr(pts, "pts"), pts.shape[0], _ptr(ext8, "ext8"), _ptr(surv_idx, "surv_idx"),
+                                     _ptr(surv_pts, "surv_pts"), _ptr(surv_count, "surv_count"), _ptr(ws, "ws"),
+                                     ws.numel(), _stream(stream)), "ch_extremes_filter")
+
+
 def ch_filter_noalloc(pts, ext8, surv_idx, surv_pts, surv_count, stream=None):
     """ch_filter without a workspace, for callers that cannot allocate device
     memory (the library's own static scratch is used; n <= 2^26; calls that
@@ -191,12 +200,13 @@ def ch_tune_get(knob: str) -> int:
 
 
 def ch_hull_counts(ws, n, stream=None):
-    """(octagon survivors, points sorted) of the last ch_hull call for n
-    points on ws (instrumentation; synchronises the stream)."""
-    out = (ctypes.c_uint32 * 2)()
+    """(octagon survivors, points sorted, speculative sweep used: 0/1) of the
+    last ch_hull call for n points on ws (instrumentation; synchronises the
+    stream)."""
+    out = (ctypes.c_uint32 * 3)()
     _check(load().ch_hull_counts(_ptr(ws, "ws"), ws.numel(), int(n), ctypes.addressof(out), _stream(stream)),
            "ch_hull_counts")
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def ch_last_error(ws, stream=None) -> int:
@@ -276,6 +286,21 @@ def filter_points(pts, ext8, ws: Workspace | None = None, with_points: bool = Tr
     cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
     ch_filter(pts, ext8, idx, sp, cnt, ws.buf)
     return idx, sp, cnt
+
+
+def extremes_and_filter(pts, ws: Workspace | None = None, with_points: bool = True):
+    """(ext8, surv_idx, surv_pts or None, count) on the device from one
+    ch_extremes_filter call; entries beyond ``count`` are unspecified."""
+    import torch
+    pts = _as_points(pts)
+    n = pts.shape[0]
+    ws = ws or Workspace(n, device=pts.device)
+    ext8 = torch.zeros(8, dtype=torch.int32, device=pts.device)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+    sp = torch.empty((max(n, 1), 2), dtype=torch.float32, device=pts.device) if with_points else None
+    cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
+    ch_extremes_filter(pts, ext8, idx, sp, cnt, ws.buf)
+    return ext8, idx, sp, cnt
 
 
 def convex_hull(pts, ws: Workspace | None = None):

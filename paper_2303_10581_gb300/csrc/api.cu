@@ -99,6 +99,27 @@ extern "C" ch_status ch_filter(const float *pts, int64_t n, const uint32_t *ext8
     return cuda_status(launch_filter(pts, n, ws, L, surv_idx, surv_pts, surv_count, false, st));
 }
 
+extern "C" ch_status ch_extremes_filter(const float *pts, int64_t n, uint32_t *ext8, uint32_t *surv_idx,
+                                        float *surv_pts, uint32_t *surv_count, void *ws, size_t ws_bytes,
+                                        void *stream)
+{
+    if (!surv_count || n < 0 || !aligned(surv_count, 4)) return CH_ERR_ARG;
+    if (n > kMaxN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(surv_count, 0, sizeof(uint32_t), st));
+    if (!pts || !ext8 || !surv_idx || !aligned(pts, 8) || !aligned(ext8, 4) || !aligned(surv_idx, 4) ||
+        (surv_pts && !aligned(surv_pts, 8)))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    const int variant = filter_variant();
+    cudaError_t e = launch_extremes(pts, n, ws, L, ext8, true, at<unsigned long long>(ws, L.ctrl),
+                                    (int64_t)L.zero_words, st, variant == 0);
+    if (e == cudaSuccess)
+        e = launch_filter(pts, n, ws, L, surv_idx, surv_pts, surv_count, false, st, variant, false, true);
+    return cuda_status(e);
+}
+
 namespace {
 
 inline bool kgon_k_ok(int32_t K) { return K == 8 || K == 16 || K == 32 || K == 64; }
@@ -163,9 +184,11 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
     if (!pts || !hull_idx || !aligned(pts, 8) || !aligned(hull_idx, 4)) return CH_ERR_ARG;
     const Layout L = make_layout(n);
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    // the two-pass schedule takes the speculative sweep's candidates
+    const int variant = filter_variant();
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
-                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st);
-    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, -1, true);
+                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0);
+    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
     if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
     return cuda_status(e);
@@ -211,12 +234,14 @@ extern "C" ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32
     const Layout L = make_layout(n);
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return CH_ERR_CUDA;
-    uint32_t sorted = 0, s_oct = 0;
+    uint32_t sorted = 0, s_oct = 0, spec = 0;
     if (cudaMemcpy(&sorted, &at<Ctrl>(ws, L.ctrl)->surv_count, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&s_oct, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_oct, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(&s_oct, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_oct, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&spec, &at<Octagon>(ws, L.oct)->spec, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CH_ERR_CUDA;
     counts[0] = s_oct ? s_oct : sorted;
     counts[1] = sorted;
+    counts[2] = spec;
     return CH_OK;
 }
 

@@ -66,7 +66,7 @@ struct Octagon {
     uint32_t valid;         // bit k: edge k has non-zero length
     uint32_t has_edges;     // at least one valid edge
     uint32_t abort;         // non-finite input: later stages do nothing
-    uint32_t pad;
+    uint32_t spec;          // 1: the speculative sweep's candidates hold every survivor (spec.cu)
     float xl, xh, yl, yh;   // closed quick-discard rectangle (xl > xh: none)
     float cx, cy;           // bounding-box centre, for the edge order
     float bxl, bxh, byl, byh;   // closed bounding box of the eight vertices
@@ -139,6 +139,26 @@ struct Ctrl {
     uint32_t pad;
 };
 
+// Speculative single sweep (extremes.cu, filter.cu): a test region from an
+// input sample; the extremes sweep keeps the points it cannot prove inside
+// it (the candidates: index in the second key buffer, point in the second
+// payload buffer).  Segment j holds the candidates of sweep block j, in
+// one slice of `cap` slots per warp.
+constexpr int kSpecMaxSeg = 2048;         // sweep blocks (segments) at most
+constexpr int kSpecWarps = kExtThreads / 32;   // slices per segment
+constexpr int kSpecCapDiv = 32;           // all slices together hold n / 32 candidates
+constexpr int kSpecKeptSmem = 2048;       // survivors per segment ranked in shared memory
+constexpr int64_t kSpecMinN = 1 << 22;    // smaller sets: the plain two passes
+struct SpecCtrl {
+    uint32_t kmax[8];                     // ord_key of the sample's largest slot keys (self-resetting)
+    uint32_t sample_done;                 // sample blocks finished
+    uint32_t fail;                        // a slice overflowed: fall back (zeroed by the sample kernel)
+    uint32_t nseg;                        // segments (sweep blocks) of this call
+    uint32_t cap;                         // candidate slots per slice
+    uint32_t scnt[kSpecMaxSeg * kSpecWarps];   // candidates written per slice
+    uint32_t skept[kSpecMaxSeg];          // survivors of the octagon per segment (their slots in utmp)
+};
+
 // persistent words: survive calls, cleared by ch_last_error
 struct Persist {
     uint32_t error;
@@ -167,6 +187,7 @@ struct Layout {
     size_t filt_bsum;       // u32[kFiltMaxBlocks]: survivors per block of the count pass
     size_t kgon;            // Kgon
     size_t utmp;          // u32[n]
+    size_t spec, p0;        // SpecCtrl, the speculative sweep's test region (SpecBox, extremes.cu)
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
 };
@@ -282,6 +303,8 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.filt_bsum = take((size_t)kFiltMaxBlocks * 4);
     L.kgon = take(sizeof(Kgon));
     L.utmp = take((size_t)n * 4);
+    L.spec = take(sizeof(SpecCtrl));
+    L.p0 = take(256);
     L.total = o;
     return L;
 }

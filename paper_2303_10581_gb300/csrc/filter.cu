@@ -386,6 +386,119 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
 }
 
 // ---------------------------------------------------------------------------
+// the speculative sweep's candidates (extremes.cu): when the sweep proved
+// every other point strictly inside the octagon (Octagon::spec), the count
+// and scatter passes test and write only the candidates.  Segment j holds
+// (unordered) the candidates of the j-th sweep block's contiguous index
+// range, so segments in order, each sorted by index, give the survivors in
+// ascending index order.
+// ---------------------------------------------------------------------------
+// Count pass: the exact test of every candidate; the slots of a segment's
+// survivors go to utmp (unordered), their number to skept, and each count
+// block's total to the block totals the fan reads.
+__device__ void spec_count(const Octagon &so, void *ws, const Layout &L, uint32_t (&s_w)[NW])
+{
+    SpecCtrl *sc = at<SpecCtrl>(ws, L.spec);
+    const float2 *cpt = at<float2>(ws, L.pay[1]);
+    uint32_t *kept_slot = at<uint32_t>(ws, L.utmp);
+    __shared__ uint32_t s_k;
+    const uint32_t nseg = sc->nseg, cap = sc->cap;
+    uint32_t block_total = 0;
+    for (uint32_t j = blockIdx.x; j < nseg; j += gridDim.x) {
+        const size_t seg0 = (size_t)j * kSpecWarps * cap;
+        __syncthreads();   // s_k of the previous segment has been read
+        if (threadIdx.x == 0) s_k = 0u;
+        __syncthreads();
+        // slot w * cap + i of the segment: candidate i of the slice of warp w
+        for (uint32_t w = 0; w < (uint32_t)kSpecWarps; ++w) {
+            const uint32_t c = min(sc->scnt[j * kSpecWarps + w], cap);
+            for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+                const float2 p = cpt[seg0 + (size_t)w * cap + i];
+                if (keep_point<false>(so, p.x, p.y)) kept_slot[seg0 + atomicAdd(&s_k, 1u)] = w * cap + i;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sc->skept[j] = s_k;
+            block_total += s_k;
+        }
+    }
+    (void)s_w;
+    if (threadIdx.x == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = block_total;
+}
+
+struct SpecScatterSmem {
+    uint32_t idx[kSpecKeptSmem];   // indices of a segment's survivors
+    uint32_t red[NW];
+};
+
+// Scatter pass: each segment's survivors, ranked by index, at the segment's
+// offset (the survivors of the segments before it); block 0 writes the
+// count.  A segment with more survivors than shared memory holds is ranked
+// from global memory (slower, same result).
+template <bool KEYS>
+__device__ void spec_scatter(SpecScatterSmem &sm, void *ws, const Layout &L, uint32_t *surv_idx, float2 *surv_pts,
+                             uint32_t *surv_count, uint32_t *out_keys, unsigned long long *out_pay)
+{
+    const SpecCtrl *sc = at<SpecCtrl>(ws, L.spec);
+    const uint32_t *cidx = at<uint32_t>(ws, L.keys[1]);
+    const float2 *cpt = at<float2>(ws, L.pay[1]);
+    const uint32_t *kept_slot = at<uint32_t>(ws, L.utmp);
+    const uint32_t nseg = sc->nseg, cap = sc->cap, tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    if (blockIdx.x == 0) {
+        uint32_t t = 0;
+        for (uint32_t i = tid; i < nseg; i += blockDim.x) t += sc->skept[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sm.red[warp] = t;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t total = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) total += sm.red[w];
+            write_count(KEYS, at<Ctrl>(ws, L.ctrl), surv_count, total);
+        }
+    }
+    for (uint32_t j = blockIdx.x; j < nseg; j += gridDim.x) {
+        const uint32_t k = sc->skept[j];   // block-uniform
+        if (k == 0u) continue;
+        // offset: survivors of the segments before j
+        uint32_t before = 0;
+        for (uint32_t i = tid; i < j; i += blockDim.x) before += sc->skept[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        __syncthreads();   // sm of the previous segment has been read
+        if (lane == 0) sm.red[warp] = before;
+        const size_t seg0 = (size_t)j * kSpecWarps * cap;
+        const bool in_smem = k <= (uint32_t)kSpecKeptSmem;
+        if (in_smem)
+            for (uint32_t e = tid; e < k; e += blockDim.x) sm.idx[e] = cidx[seg0 + kept_slot[seg0 + e]];
+        __syncthreads();
+        uint32_t off = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) off += sm.red[w];
+        for (uint32_t e = tid; e < k; e += blockDim.x) {
+            const uint32_t slot = kept_slot[seg0 + e];
+            const uint32_t mine = cidx[seg0 + slot];
+            uint32_t r = 0;
+            if (in_smem)
+                for (uint32_t q = 0; q < k; ++q) r += sm.idx[q] < mine ? 1u : 0u;
+            else
+                for (uint32_t q = 0; q < k; ++q) r += cidx[seg0 + kept_slot[seg0 + q]] < mine ? 1u : 0u;
+            const float2 p = cpt[seg0 + slot];
+            const size_t pos = (size_t)off + r;
+            if constexpr (KEYS) {
+                out_keys[pos] = ord_key(p.x);
+                out_pay[pos] = ((unsigned long long)ord_key(p.y) << 32) | mine;
+            } else {
+                surv_idx[pos] = mine;
+                if (surv_pts) surv_pts[pos] = p;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // two passes: count -> scan -> scatter
 // ---------------------------------------------------------------------------
 // filt_status[t] receives the survivor count of tile t (low 32 bits); the
@@ -400,6 +513,12 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
     queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_w[NW];
     if (!load_octagon(so, ws, L)) return;
+    if constexpr (!BOX) {
+        if (so.spec) {   // the speculative sweep proved all but its candidates inside
+            spec_count(so, ws, L, s_w);
+            return;
+        }
+    }
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     const int64_t ntiles = ceil_div(n, kFiltTile);
@@ -444,7 +563,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
                                                                       void *ws, Layout L,
                                                                       uint32_t *__restrict__ surv_idx,
                                                                       float2 *__restrict__ surv_pts,
-                                                                      uint32_t *surv_count)
+                                                                      uint32_t *surv_count, int allow_spec)
 {
     __shared__ uint32_t s_off[kFiltItems / G][NW];
     __shared__ uint32_t s_abort;
@@ -452,11 +571,22 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
     __shared__ uint32_t s_list[kFiltThreads];    // non-empty tiles of a chunk: offset in chunk
     __shared__ uint32_t s_loff[kFiltThreads];    // and their output offsets
     __shared__ uint32_t s_nlist;
+    __shared__ uint32_t s_spec;
+    __shared__ SpecScatterSmem s_sp;
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
-    if (threadIdx.x == 0) s_abort = at<Octagon>(ws, L.oct)->abort;
+    if (threadIdx.x == 0) {
+        const Octagon *oct = at<Octagon>(ws, L.oct);
+        s_abort = oct->abort;
+        s_spec = allow_spec ? oct->spec : 0u;   // a polygon the octagon record does not describe: never
+    }
     __syncthreads();
     if (s_abort) {
         if (blockIdx.x == 0 && threadIdx.x == 0) write_count(KEYS, ctrl, surv_count, 0);
+        return;
+    }
+    if (s_spec) {   // only the speculative sweep's candidates can survive
+        spec_scatter<KEYS>(s_sp, ws, L, surv_idx, surv_pts, surv_count, at<uint32_t>(ws, L.keys[0]),
+                           at<unsigned long long>(ws, L.pay[0]));
         return;
     }
     const unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
@@ -819,16 +949,20 @@ cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L
     return cudaGetLastError();
 }
 
-template <int G, bool KEYS>
+// BOX: the polygon's vertices were supplied by the caller (ch_filter), so
+// points outside their box must be kept first; otherwise they are the
+// data's extremes, and the scatter may take the speculative sweep's
+// candidates (Octagon::spec)
+template <int G, bool KEYS, bool BOX>
 cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                             float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan)
 {
-    static int per_sm_c = occupancy(filter_count_kernel<G, !KEYS>, kFiltThreads);
+    static int per_sm_c = occupancy(filter_count_kernel<G, BOX>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
     // both passes use the same grid: block b owns the same tile range
     const int64_t bc = std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
-    filter_count_kernel<G, !KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    filter_count_kernel<G, BOX><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
     if (fan) {   // timed as its own group, between the filter's two
         probe_after(CH_K_FILTER, st);
         const cudaError_t e = launch_fan(pts, n, G == 2, bc, ws, L, st);
@@ -836,7 +970,7 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
         probe_before(CH_K_FILTER, st);
     }
     filter_scatter_kernel<G, KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(
-        pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count);
+        pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count, BOX ? 0 : 1);
     note_kernels(CH_K_FILTER, 2);
     return cudaGetLastError();
 }
@@ -848,29 +982,34 @@ std::atomic<int> g_filter_variant{0};
 
 template <int G, bool KEYS>
 cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                           float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant, bool fan)
+                           float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant, bool fan,
+                           bool data_extremes)
 {
     probe_before(CH_K_FILTER, st);
-    const cudaError_t e = variant == 1
-                              ? launch_single<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st)
-                              : launch_two_pass<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
+    cudaError_t e;
+    if (variant == 1) e = launch_single<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st);
+    else if (KEYS || data_extremes)
+        e = launch_two_pass<G, KEYS, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
+    else e = launch_two_pass<G, false, true>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
     probe_after(CH_K_FILTER, st);
     return e;
 }
 
 }  // namespace
 
+int filter_variant() { return g_filter_variant.load(std::memory_order_relaxed); }
+
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant,
-                          bool fan)
+                          bool fan, bool data_extremes)
 {
     const int v = variant < 0 ? g_filter_variant.load(std::memory_order_relaxed) : variant;
     const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
     if (keys_mode)
-        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan)
-                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan);
-    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false)
-               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false);
+        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true)
+                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true);
+    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes)
+               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes);
 }
 
 cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, void *ws, const Layout &L,
@@ -881,11 +1020,11 @@ cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, voi
     float2 *sp = reinterpret_cast<float2 *>(surv_pts);
     const unsigned g = (unsigned)std::max<int64_t>(1, grid);
     if (keys_mode) {
-        if (vec) filter_scatter_kernel<2, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr);
-        else filter_scatter_kernel<1, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr);
+        if (vec) filter_scatter_kernel<2, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr, 0);
+        else filter_scatter_kernel<1, true><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, nullptr, nullptr, nullptr, 0);
     } else {
-        if (vec) filter_scatter_kernel<2, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count);
-        else filter_scatter_kernel<1, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count);
+        if (vec) filter_scatter_kernel<2, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count, 0);
+        else filter_scatter_kernel<1, false><<<g, kFiltThreads, 0, st>>>(pts, n, ws, L, surv_idx, sp, surv_count, 0);
     }
     note_kernels(CH_K_FILTER, 1);
     return cudaGetLastError();

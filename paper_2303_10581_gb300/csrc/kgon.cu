@@ -121,7 +121,7 @@ __device__ __forceinline__ bool fan_inside(const float2 *V, float cx, float cy, 
 __device__ __forceinline__ bool fan_live(const KgonCtrl *kc, const Octagon *oct, uint32_t &s)
 {
     s = oct->abort ? 0u : kc->s_oct;
-    return s >= kKgonMinS && oct->has_edges;
+    return s >= kKgonMinS && oct->has_edges && !oct->spec;   // spec: no keep bits to refine
 }
 
 // bc: the grid of the filter's count pass (its block totals are in
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     uint32_t s = 0;
     for (int w = 0; w < FT / 32; ++w) s += s_red[w];
     if (blockIdx.x == 0 && threadIdx.x == 0) kc->s_oct = s;
-    if (s < kKgonMinS || !oct->has_edges) return;
+    if (s < kKgonMinS || !oct->has_edges || oct->spec) return;
     for (int i = threadIdx.x; i < kFanBins; i += FT) s_best[i] = 0ull;
     __syncthreads();
     const float cx = oct->cx, cy = oct->cy;

@@ -17,9 +17,13 @@ void probe_before(int kid, cudaStream_t st);
 void note_kernels(int kid, int count);
 void probe_after(int kid, cudaStream_t st);
 
+// spec (with build_polygon, on large sets): the speculative single sweep --
+// a sample octagon first, then the sweep writes the points it cannot prove
+// inside it as candidates; when its last block proves the sample octagon
+// inside the final one (Octagon::spec), the filter's passes test only them
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
-                            cudaStream_t st);
+                            cudaStream_t st, bool spec = false);
 
 cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, void *ws, const Layout &L,
                            unsigned long long *zero_ptr, int64_t zero_words, cudaStream_t st);
@@ -28,10 +32,16 @@ cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, vo
 // pairs into the sort buffers of ws instead of (index, point) outputs.
 // variant: 0 two passes (needs keep_bits in L), 1 single pass, -1 the
 // process-wide choice of ch_filter_variant.  fan (hull step, two passes
-// only): launch_fan between the count and the scatter pass.
+// only): launch_fan between the count and the scatter pass.  data_extremes:
+// the polygon was built from the data's own extremes (ch_hull,
+// ch_extremes_filter; always so in keys mode), which allows the speculative
+// sweep's candidates; otherwise the vertices are the caller's (ch_filter).
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
-                          int variant = -1, bool fan = false);
+                          int variant = -1, bool fan = false, bool data_extremes = false);
+
+// the process-wide compaction schedule (ch_filter_variant)
+int filter_variant();
 
 // the filter's scatter pass alone, on keep bits, tile counts and block
 // totals that a count pass of `grid` blocks (same layout as the filter's)

@@ -60,6 +60,8 @@ static void check_single(int64_t n, int64_t sets)
         {"filt_bsum", L.filt_bsum, (size_t)kFiltMaxBlocks * 4},
         {"kgon", L.kgon, sizeof(Kgon)},
         {"utmp", L.utmp, nn * 4},
+        {"spec", L.spec, sizeof(SpecCtrl)},
+        {"p0", L.p0, 256},
     };
     for (size_t i = 0; i < r.size(); ++i) {
         CHECK(r[i].at % 256 == 0, "n=%lld sets=%lld: %s not 256-aligned", (long long)n, (long long)sets, r[i].name);

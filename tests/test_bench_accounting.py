@@ -32,9 +32,13 @@ def one_device(monkeypatch):
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: Props())
 
 
-def test_alu_roofline_counts_fan_sets_only(one_device):
-    rec = bench.load_traffic("kgon")
-    assert rec is not None, "profiles/traffic.json must describe the current kgon.cu"
+FAN_RECORD = {"source": "kgon.cu", "capture": "test record", "dram_per_algorithmic_byte": 1.25,
+              "warp_inst_per_survivor": 4.5}
+
+
+def test_alu_roofline_counts_fan_sets_only(one_device, monkeypatch):
+    monkeypatch.setattr(bench, "load_traffic", lambda kernel: FAN_RECORD if kernel == "kgon" else None)
+    rec = FAN_RECORD
     steps, launches, ms = 5, 60, 6.0
     r = bench.alu_roofline(ms, launches, steps, N, S, T, {"sm_max_mhz": 2070.0}, None)
     inst = rec["warp_inst_per_survivor"] * (S[1] + S[2]) * steps
@@ -43,6 +47,11 @@ def test_alu_roofline_counts_fan_sets_only(one_device):
     assert r["achieved"] == pytest.approx(inst / (ms * 1e-3) / 1e12, abs=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], abs=1e-3)
     assert r["warp_instr_per_launch"] == int(inst / launches)
+    # the same launches against the HBM roofline: 8 B per octagon survivor tested
+    hbm_peak, _ = bench.peaks()
+    gbs = 8 * (S[1] + S[2]) * steps / launches / (ms / launches * 1e-3) / 1e9
+    assert r["hbm_achieved_gbs"] == pytest.approx(gbs, abs=0.1)
+    assert r["hbm_frac"] == pytest.approx(gbs / hbm_peak, abs=1e-3)
 
 
 def test_alu_roofline_void_when_source_changed(one_device, monkeypatch):
