@@ -165,11 +165,15 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline bookkeeping
 
+SMALL_HULL = 512   # at most this many points to sort: one block sorts and chains them (no sort passes)
+
+
 def algorithmic_bytes(kernel, n, s_list, t_list):
     """Bytes a kernel must move in one step (all its launches for the step's
     sets), from the data it reads and writes by definition; s_list holds the
     octagon-filter survivors of each set, t_list the points the hull step
-    sorts (the survivors of the fan test as well, when it ran)."""
+    sorts (the survivors of the fan test as well, when it ran).  Sets with
+    at most SMALL_HULL points to sort run no sort and chain kernels."""
     if kernel == "extremes":
         return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
@@ -178,14 +182,15 @@ def algorithmic_bytes(kernel, n, s_list, t_list):
         # the fan test of the octagon survivors when it ran (read their
         # coordinates); otherwise only samples
         return sum(8 * s if t < s else 0 for s, t in zip(s_list, t_list))
+    big = [t for t in t_list if t > SMALL_HULL]
     if kernel == "sort_hist":
-        return sum(4 * t for t in t_list)                   # read the 32-bit keys
+        return sum(4 * t for t in big)                      # read the 32-bit keys
     if kernel == "sort_pass":
-        # 4 passes (32-bit x key) per set with more than one point; each
-        # reads and writes key (4 B) + payload (8 B): 24 B per point
-        return sum(4 * 24 * t for t in t_list if t > 1)
+        # 4 passes (32-bit x key) per set; each reads and writes key (4 B)
+        # + payload (8 B): 24 B per point
+        return sum(4 * 24 * t for t in big)
     if kernel == "chain":
-        return sum(12 * t for t in t_list)                  # read the sorted keys and payloads once
+        return sum(12 * t for t in big)                     # read the sorted keys and payloads once
     return None
 
 

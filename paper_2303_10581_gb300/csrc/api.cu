@@ -169,6 +169,7 @@ extern "C" ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs
         e = launch_filter_scatter(pts, n, grid, ws, L, nullptr, nullptr, nullptr, true, st);
         probe_after(CH_K_FILTER, st);
     }
+    if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
     if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
     return cuda_status(e);
@@ -189,6 +190,7 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
                                     at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0);
     if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true);
+    if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
     if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
     return cuda_status(e);

@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(LT) chain_kernel(void *ws, Layout L)
     ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    const uint32_t s = hull_stage_count(ctrl, oct);
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     const int64_t nsc = ceil_div((int64_t)s, SC);
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(32) chain_merge_kernel(void *ws, Layout L)
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    const uint32_t s = hull_stage_count(ctrl, oct);
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     const int64_t nsc = ceil_div((int64_t)s, SC);
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    const uint32_t s = hull_stage_count(ctrl, oct);
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
     EmitArgs E{{hull_idx, at<uint32_t>(ws, L.utmp)}, {nullptr, nullptr}, &ctrl->emit_ticket[0],
@@ -972,6 +972,7 @@ __global__ void __launch_bounds__(kEmitThreads) bx_emit_kernel(void *ws, Layout 
 __global__ void finish_kernel(void *ws, Layout L, uint32_t *hull_idx, uint32_t *hull_count)
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    if (ctrl->small_done) return;
     const uint32_t hl = ctrl->h_lower, hu = ctrl->h_upper;
     const uint32_t mid = hu >= 2 ? hu - 2 : 0;
     const uint32_t *utmp = at<uint32_t>(ws, L.utmp);
@@ -981,7 +982,105 @@ __global__ void finish_kernel(void *ws, Layout L, uint32_t *hull_idx, uint32_t *
     if (blockIdx.x == 0 && threadIdx.x == 0) *hull_count = hl == 0 ? 0u : hl + mid;
 }
 
+// Few survivors (at most kSmallHull): one block sorts them by (x, y, index)
+// in shared memory (bitonic network over the packed keys and indices),
+// then one thread runs Andrew's monotone chain over them -- equal points
+// collapse to the first, a turn that is not strictly counter-clockwise
+// (exact sign) pops the middle point -- and writes the hull, counter-
+// clockwise from the first point; the sort and chain kernels launched
+// after it then stop at once.  More survivors: it does nothing.
+constexpr int kSmallHull = 512;
+constexpr int kSmallThreads = 256;
+
+__global__ void __launch_bounds__(kSmallThreads) small_hull_kernel(void *ws, Layout L, uint32_t *hull_idx,
+                                                                   uint32_t *hull_count)
+{
+    Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const uint32_t s = hull_stage_count(ctrl, oct);
+    if (s == 0 || s > (uint32_t)kSmallHull) return;
+    __shared__ unsigned long long sk[kSmallHull];   // ord(x) << 32 | ord(y)
+    __shared__ uint32_t si[kSmallHull];             // point index
+    __shared__ uint16_t st[2 * kSmallHull + 2];     // chain stack: sorted positions
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[ctrl->sort_in]);
+    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[ctrl->sort_in]);
+    uint32_t m = 32;
+    while (m < s) m <<= 1;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        if (i < s) {
+            const unsigned long long pv = pay[i];
+            sk[i] = ((unsigned long long)keys[i] << 32) | (pv >> 32);
+            si[i] = (uint32_t)pv;
+        } else {
+            sk[i] = ~0ull;   // after every point
+            si[i] = ~0u;
+        }
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = sk[i] > sk[l] || (sk[i] == sk[l] && si[i] > si[l]);
+                    if (gt == up) {
+                        const unsigned long long tk = sk[i];
+                        sk[i] = sk[l];
+                        sk[l] = tk;
+                        const uint32_t ti = si[i];
+                        si[i] = si[l];
+                        si[l] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x != 0) return;
+    // equal points: the first (lowest index) stays
+    uint32_t u = 0;
+    for (uint32_t i = 0; i < s; ++i) {
+        if (u > 0 && sk[i] == sk[u - 1]) continue;
+        sk[u] = sk[i];
+        si[u] = si[i];
+        ++u;
+    }
+    auto px = [&](uint32_t k) { return key_float((uint32_t)(sk[k] >> 32)); };
+    auto py = [&](uint32_t k) { return key_float((uint32_t)sk[k]); };
+    uint32_t h = 0;
+    if (u == 1) {
+        hull_idx[0] = si[0];
+        h = 1;
+    } else {
+        for (uint32_t k = 0; k < u; ++k) {   // lower chain, left to right
+            while (h >= 2 && orient(px(st[h - 2]), py(st[h - 2]), px(st[h - 1]), py(st[h - 1]), px(k), py(k)) <= 0)
+                --h;
+            st[h++] = (uint16_t)k;
+        }
+        const uint32_t base = h + 1;
+        for (int k = (int)u - 2; k >= 0; --k) {   // upper chain, right to left
+            while (h >= base && orient(px(st[h - 2]), py(st[h - 2]), px(st[h - 1]), py(st[h - 1]), px(k), py(k)) <= 0)
+                --h;
+            st[h++] = (uint16_t)k;
+        }
+        --h;   // the last point is the first again
+        for (uint32_t k = 0; k < h; ++k) hull_idx[k] = si[st[k]];
+    }
+    *hull_count = h;
+    ctrl->small_done = 1u;
+}
+
 }  // namespace
+
+cudaError_t launch_small_hull(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st)
+{
+    probe_before(CH_K_CHAIN, st);
+    small_hull_kernel<<<1, kSmallThreads, 0, st>>>(ws, L, hull_idx, hull_count);
+    note_kernels(CH_K_CHAIN, 1);
+    probe_after(CH_K_CHAIN, st);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st)
 {

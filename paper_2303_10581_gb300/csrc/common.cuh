@@ -136,8 +136,15 @@ struct Ctrl {
     uint32_t emit_ticket[2];
     uint32_t h_lower, h_upper;
     uint32_t sort_in;                 // buffer holding the survivors for the sort (the filter writes buffer 0)
-    uint32_t pad;
+    uint32_t small_done;              // the one-block hull of few survivors wrote the hull: later kernels stop
 };
+
+// Points the sort and chain kernels of a single-set hull work on: none
+// when the call was aborted or the one-block hull already finished it.
+__device__ __forceinline__ uint32_t hull_stage_count(const Ctrl *ctrl, const Octagon *oct)
+{
+    return (oct->abort || ctrl->small_done) ? 0u : ctrl->surv_count;
+}
 
 // Speculative single sweep (extremes.cu, filter.cu): a test region from an
 // input sample; the extremes sweep keeps the points it cannot prove inside

@@ -402,20 +402,36 @@ __device__ void spec_count(const Octagon &so, void *ws, const Layout &L, uint32_
     const float2 *cpt = at<float2>(ws, L.pay[1]);
     uint32_t *kept_slot = at<uint32_t>(ws, L.utmp);
     __shared__ uint32_t s_k;
+    __shared__ uint32_t s_pre[kSpecWarps + 1];   // candidates before each slice of the segment
     const uint32_t nseg = sc->nseg, cap = sc->cap;
     uint32_t block_total = 0;
     for (uint32_t j = blockIdx.x; j < nseg; j += gridDim.x) {
         const size_t seg0 = (size_t)j * kSpecWarps * cap;
-        __syncthreads();   // s_k of the previous segment has been read
-        if (threadIdx.x == 0) s_k = 0u;
-        __syncthreads();
-        // slot w * cap + i of the segment: candidate i of the slice of warp w
-        for (uint32_t w = 0; w < (uint32_t)kSpecWarps; ++w) {
-            const uint32_t c = min(sc->scnt[j * kSpecWarps + w], cap);
-            for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
-                const float2 p = cpt[seg0 + (size_t)w * cap + i];
-                if (keep_point<false>(so, p.x, p.y)) kept_slot[seg0 + atomicAdd(&s_k, 1u)] = w * cap + i;
+        __syncthreads();   // s_k and s_pre of the previous segment have been read
+        if (threadIdx.x < 32) {
+            const uint32_t c = threadIdx.x < (uint32_t)kSpecWarps ? min(sc->scnt[j * kSpecWarps + threadIdx.x], cap) : 0u;
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (threadIdx.x >= (uint32_t)o) incl += t;
             }
+            if (threadIdx.x < (uint32_t)kSpecWarps) s_pre[threadIdx.x + 1] = incl;
+            if (threadIdx.x == 0) {
+                s_pre[0] = 0u;
+                s_k = 0u;
+            }
+        }
+        __syncthreads();
+        // the segment's candidates in one sweep: e-th candidate = candidate
+        // e - s_pre[w] of the slice of warp w, at slot w * cap + that
+        const uint32_t total = s_pre[kSpecWarps];
+        for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+            uint32_t w = 0;
+            while (s_pre[w + 1] <= e) ++w;
+            const uint32_t slot = w * cap + (e - s_pre[w]);
+            const float2 p = cpt[seg0 + slot];
+            if (keep_point<false>(so, p.x, p.y)) kept_slot[seg0 + atomicAdd(&s_k, 1u)] = slot;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -9,7 +9,8 @@
 // centre of the bounding box, checked with exact signs to lie strictly
 // inside the octagon, hence strictly inside the hull.  The plane around c
 // is cut into kFanBins angular bins; the vertex of a bin is the input point
-// farthest from c among a sample (every 4th 4096-point tile of the input),
+// farthest from c among a sample (about kBinTiles evenly spaced 4096-point
+// tiles of the input),
 // and a bin the sample missed repeats the vertex before it.  For
 // consecutive vertices v, w every point strictly inside the triangle
 // (c, v, w) is a combination of c, v and w with positive weights, so it
@@ -48,7 +49,7 @@ constexpr int FITEMS = 8;                // points per thread per tile there
 constexpr int FTILE = FT * FITEMS;       // 4096
 constexpr int CT = 1024;                 // threads per block of the refine pass: four
 constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, each with its own tiles
-constexpr int kTileSample = 4;           // the bins see every 4th tile
+constexpr int64_t kBinTiles = 6144;      // the bins see about this many evenly spaced tiles (25 M points)
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
 static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
@@ -152,11 +153,12 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     __syncthreads();
     const float cx = oct->cx, cy = oct->cy;
     const int64_t ntiles = ceil_div(n, FTILE);
-    const int64_t nsamp = ceil_div(ntiles, kTileSample);
+    const int64_t stride = std::max<int64_t>(1, ntiles / kBinTiles);   // every stride-th tile
+    const int64_t nsamp = ceil_div(ntiles, stride);
     for (int64_t k = blockIdx.x; k < nsamp; k += gridDim.x) {
-        const int64_t base = k * kTileSample * FTILE;
+        const int64_t base = k * stride * FTILE;
         if (threadIdx.x == 0 && k + gridDim.x < nsamp) {   // this block's next sample tile streams into L2
-            const int64_t nb = (k + gridDim.x) * kTileSample * FTILE;
+            const int64_t nb = (k + gridDim.x) * stride * FTILE;
             const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, n - nb);
             if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
         }

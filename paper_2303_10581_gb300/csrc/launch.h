@@ -66,6 +66,10 @@ cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const 
 cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blocks, void *ws, const Layout &L,
                        cudaStream_t st);
 
+// the whole hull in one block when few points survived the filter (the
+// sort and chain kernels then stop at once); otherwise nothing
+cudaError_t launch_small_hull(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t *hull_count, cudaStream_t st);
+
 // stable LSD radix sort of the survivor (key, index) pairs held in ws
 cudaError_t launch_sort(void *ws, const Layout &L, cudaStream_t st);
 

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(void *ws, Layout L)
 {
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    const uint32_t s = hull_stage_count(ctrl, oct);
     const int64_t ntiles = ceil_div((int64_t)s, kSortTile);
     // the first executed pass reads the survivors' buffer and its status
     uint32_t *status0 = at<uint32_t>(ws, L.sort_status[ctrl->sort_in]);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel(void *ws, La
     SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
     Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const uint32_t s = oct->abort ? 0u : ctrl->surv_count;
+    const uint32_t s = hull_stage_count(ctrl, oct);
     if (s == 0 || ctrl->pass_skip[p]) return;
     const uint32_t src = ctrl->pass_src[p], dst = src ^ 1u;
     const int64_t ntiles = ceil_div((int64_t)s, kSortTile);
