@@ -237,8 +237,12 @@ struct BatchCtrl {
     uint32_t filt_ticket, emit_ticket, pad0;
     uint32_t sort_ticket[kSortPasses];
     uint32_t h_lower, h_upper;
-    uint32_t pad[4];
+    uint32_t nfan;        // sets that get the fan test (kgon.cu)
+    uint32_t nitems;      // the fan refine's work items (a set's run of up to kBxFanChunk tiles)
+    uint32_t fan_ticket;  // next work item of the fan refine
+    uint32_t pad;
 };
+constexpr int kBxFanChunk = 64;       // tiles per work item of the batched fan refine
 
 // Extra workspace of ch_hull_batched, after the single-set regions.
 struct BatchLayout {
@@ -254,8 +258,17 @@ struct BatchLayout {
     size_t sc_set;        // u32[tiles_max]: set of each super-chunk
     size_t sc_off[2];     // u32[tiles_max + 1]: lower / upper chain offset of each super-chunk
     size_t lower;         // u32[n]: lower chains of all sets (set-local indices); aliases keys[1]
+    // the fan of the hull step, per set with many octagon survivors (kgon.cu)
+    size_t soct;          // u32[B]: octagon survivors per set (in the zeroed range)
+    size_t fan_id;        // i32[B]: the set's fan number, -1: none
+    size_t fan_set;       // u32[max_fan]: set of each fan
+    size_t fan_ok;        // u32[max_fan]: the fan has vertices and its centre is inside
+    size_t fan_c;         // float2[max_fan]: centre
+    size_t fan_slot;      // u64[max_fan * kFanBins]: farthest sampled point per bin (left zeroed)
+    size_t fan_v;         // float2[max_fan * kFanBins]: vertices
+    size_t fan_items;     // uint2[max_items]: (fan, first tile) of each refine work item
     size_t total;
-    int64_t num_sets, tiles_max;
+    int64_t num_sets, tiles_max, max_fan, max_items;
 };
 
 __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
@@ -334,12 +347,23 @@ __host__ __device__ inline BatchLayout make_batch_layout(const Layout &L, int64_
     B.ext_slot = take((size_t)sets * 8 * 8);
     B.nonfinite = take((size_t)sets * 4);
     B.hist = take((size_t)sets * kSortPasses * 256 * 4);
+    B.soct = take((size_t)sets * 4);
     B.zero_end = o;
     B.tile_set = take((size_t)B.tiles_max * 4);
     B.sc_set = take((size_t)B.tiles_max * 4);
     B.sc_off[0] = take((size_t)(B.tiles_max + 1) * 4);
     B.sc_off[1] = take((size_t)(B.tiles_max + 1) * 4);
     B.lower = L.keys[1];   // the second sort buffer is free once the sort ends in buffer 0
+    // a set with a fan has at least 2^16 points
+    B.max_fan = sets < L.n / 65536 + 1 ? sets : L.n / 65536 + 1;
+    B.max_items = B.tiles_max / kBxFanChunk + B.max_fan + 1;
+    B.fan_id = take((size_t)sets * 4);
+    B.fan_set = take((size_t)B.max_fan * 4);
+    B.fan_ok = take((size_t)B.max_fan * 4);
+    B.fan_c = take((size_t)B.max_fan * 8);
+    B.fan_slot = take((size_t)B.max_fan * kFanBins * 8);
+    B.fan_v = take((size_t)B.max_fan * kFanBins * 8);
+    B.fan_items = take((size_t)B.max_items * 8);
     B.total = o;
     return B;
 }

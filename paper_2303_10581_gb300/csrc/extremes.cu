@@ -739,6 +739,50 @@ __global__ void octagon_kernel(const float *__restrict__ pts, int64_t n, const u
 // set, finished with per-set packed atomics; then one warp per set builds
 // its polygon.  Indices are set-local.
 // ---------------------------------------------------------------------------
+// Each block takes a contiguous range of tiles; the running extremes are
+// folded into the set's slots whenever the range moves on to another set
+// (sets are contiguous in tile order, so a block flushes once per set it
+// touches).
+__device__ __forceinline__ void bx_flush(Best &best, float &nf, int64_t b, unsigned long long *slots,
+                                         uint32_t *nonfin, float (&sk)[8][8], uint32_t (&si)[8][8], int &s_bad)
+{
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float ok = __shfl_xor_sync(0xffffffffu, best.k[j], o);
+            const uint32_t oi = __shfl_xor_sync(0xffffffffu, best.i[j], o);
+            combine(best.k[j], best.i[j], ok, oi);
+        }
+    }
+    __syncthreads();   // sk, si and s_bad of the previous flush have been read
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    if (nf != nf) s_bad = 1;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sk[warp][j] = best.k[j];
+            si[warp][j] = best.i[j];
+        }
+    __syncthreads();
+    if (warp == 0 && lane < 8) {
+        float k = sk[0][lane];
+        uint32_t i = si[0][lane];
+        for (int w = 1; w < 8; ++w) combine(k, i, sk[w][lane], si[w][lane]);
+        if (i != 0xffffffffu)
+            atomicMax(&slots[(size_t)b * 8 + lane], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
+        if (lane == 0 && s_bad) atomicOr(&nonfin[b], 1u);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        best.k[j] = __int_as_float(0x7fc00000);
+        best.i[j] = 0xffffffffu;
+    }
+    nf = 0.0f;
+}
+
 __global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restrict__ pts, void *ws, Layout L,
                                                           BatchLayout BL)
 {
@@ -751,54 +795,52 @@ __global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restric
     __shared__ float sk[8][8];
     __shared__ uint32_t si_[8][8];
     __shared__ int s_bad;
-    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    const uint32_t T = bc->tiles;
-    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
-        const uint32_t b = tile_set[t];
-        const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
+    const int64_t T = bc->tiles;
+    const int64_t per = ceil_div(T, (int64_t)gridDim.x);
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
+    constexpr int R = kFiltTile / 256;   // points per thread per tile
+    Best best;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        best.k[j] = __int_as_float(0x7fc00000);
+        best.i[j] = 0xffffffffu;
+    }
+    float nf = 0.0f;
+    int64_t cur = -1;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t b = tile_set[t];   // block-uniform
+        if (b != cur) {
+            if (cur >= 0) bx_flush(best, nf, cur, slots, nonfin, sk, si_, s_bad);
+            cur = b;
+        }
+        const int64_t lo = (t - sets[b].tile_base) * (int64_t)kFiltTile;
         const int64_t hi = min(lo + kFiltTile, sets[b].n);
         const float2 *p2 = reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin;
-        Best best;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            best.k[j] = __int_as_float(0x7fc00000);
-            best.i[j] = 0xffffffffu;
+        if (threadIdx.x == 0 && t + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const int64_t nb = tile_set[t + 1];
+            const int64_t nlo = (t + 1 - sets[nb].tile_base) * (int64_t)kFiltTile;
+            const int64_t nhi = min(nlo + kFiltTile, sets[nb].n);
+            const float2 *np = reinterpret_cast<const float2 *>(pts) + sets[nb].pt_begin;
+            const uintptr_t a0 = (reinterpret_cast<uintptr_t>(np + nlo) + 15) & ~(uintptr_t)15;
+            const uintptr_t a1 = reinterpret_cast<uintptr_t>(np + nhi) & ~(uintptr_t)15;
+            if (a1 > a0) bulk_prefetch_l2(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
         }
-        float nf = 0.0f;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const float2 v = __ldcs(p2 + i);
-            nf = __fmaf_rn(v.x, 0.0f, __fmaf_rn(v.y, 0.0f, nf));
-            consider(best, v.x, v.y, (uint32_t)i);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = lo + r * 256 + threadIdx.x;
+            v[r] = i < hi ? __ldcs(p2 + i) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float ok = __shfl_xor_sync(0xffffffffu, best.k[j], o);
-                const uint32_t oi = __shfl_xor_sync(0xffffffffu, best.i[j], o);
-                combine(best.k[j], best.i[j], ok, oi);
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = lo + r * 256 + threadIdx.x;
+            if (i < hi) {
+                nf = __fmaf_rn(v[r].x, 0.0f, __fmaf_rn(v[r].y, 0.0f, nf));
+                consider(best, v[r].x, v[r].y, (uint32_t)i);
             }
         }
-        if (threadIdx.x == 0) s_bad = 0;
-        __syncthreads();
-        if (nf != nf) s_bad = 1;
-        if (lane == 0)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                sk[warp][j] = best.k[j];
-                si_[warp][j] = best.i[j];
-            }
-        __syncthreads();
-        if (warp == 0 && lane < 8) {
-            float k = sk[0][lane];
-            uint32_t i = si_[0][lane];
-            for (int w = 1; w < 8; ++w) combine(k, i, sk[w][lane], si_[w][lane]);
-            if (i != 0xffffffffu)
-                atomicMax(&slots[(size_t)b * 8 + lane], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
-            if (lane == 0 && s_bad) atomicOr(&nonfin[b], 1u);
-        }
-        __syncthreads();
     }
+    if (cur >= 0) bx_flush(best, nf, cur, slots, nonfin, sk, si_, s_bad);
 }
 
 __global__ void __launch_bounds__(256) bx_octagon_kernel(const float *__restrict__ pts, void *ws, Layout L,

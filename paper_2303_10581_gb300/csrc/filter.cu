@@ -777,12 +777,26 @@ __global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const flo
     const Octagon *octs = at<Octagon>(ws, BL.octs);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    uint32_t *soct = at<uint32_t>(ws, BL.soct);
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    const uint32_t T = bc->tiles;
+    // a contiguous range of tiles per block: the polygon is loaded once per
+    // set the range touches
+    const int64_t T = bc->tiles;
+    const int64_t per = ceil_div(T, (int64_t)gridDim.x);
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
     int64_t cur = -1;
-    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+    for (int64_t t = t0; t < t1; ++t) {
         const int64_t b = tile_set[t];
         bx_octagon_to_smem(so, cur, b, octs);
+        if (threadIdx.x == 0 && t + 1 < t1) {   // the next tile streams into L2 meanwhile
+            const int64_t nb = tile_set[t + 1];
+            const int64_t nlo = (t + 1 - sets[nb].tile_base) * (int64_t)kFiltTile;
+            const int64_t nhi = min(nlo + kFiltTile, sets[nb].n);
+            const float2 *np = reinterpret_cast<const float2 *>(pts) + sets[nb].pt_begin;
+            const uintptr_t a0 = (reinterpret_cast<uintptr_t>(np + nlo) + 15) & ~(uintptr_t)15;
+            const uintptr_t a1 = reinterpret_cast<uintptr_t>(np + nhi) & ~(uintptr_t)15;
+            if (a1 > a0) bulk_prefetch_l2(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
+        }
         uint32_t keep = 0;
         if (!so.abort) {
             const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
@@ -802,6 +816,7 @@ __global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const flo
 #pragma unroll
             for (int w = 0; w < NW; ++w) sum += s_w[w];
             status[t] = sum;
+            if (sum) atomicAdd(&soct[b], sum);
         }
         __syncthreads();
     }
@@ -1055,6 +1070,12 @@ cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const 
     const int64_t bs = std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * (tuned ? tuned : per_sm_s), BL.tiles_max));
     probe_before(CH_K_FILTER, st);
     bx_filter_count_kernel<<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, ws, L, BL);
+    // the hull step's fan for the sets with many octagon survivors, timed
+    // as its own group between the count pass and the scan
+    probe_after(CH_K_FILTER, st);
+    const cudaError_t e = launch_bx_fan(pts, ws, L, BL, st);
+    if (e != cudaSuccess) return e;
+    probe_before(CH_K_FILTER, st);
     bx_filter_scan_kernel<<<1, 1024, 0, st>>>(ws, L, BL);
     bx_filter_scatter_kernel<<<(unsigned)bs, kFiltThreads, 0, st>>>(pts, ws, L, BL);
     note_kernels(CH_K_FILTER, 3);

@@ -461,4 +461,309 @@ cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blo
     return cudaGetLastError();
 }
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// many sets (ch_hull_batched): the same fan for every set with at least
+// kKgonMinS octagon survivors, between the batched count pass and its scan
+// ---------------------------------------------------------------------------
+constexpr int kBxBinStride = 2;   // the bins see every 2nd tile of a set (1 and 4 measured slower overall)
+
+// One block: numbers the sets that get a fan and lays out the refine's
+// work items (runs of up to kBxFanChunk tiles of one such set).
+__global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L, BatchLayout BL)
+{
+    __shared__ uint32_t s_w[2][32];
+    BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const Octagon *octs = at<Octagon>(ws, BL.octs);
+    const uint32_t *soct = at<uint32_t>(ws, BL.soct);
+    const uint32_t *nonfin = at<uint32_t>(ws, BL.nonfinite);
+    int32_t *fan_id = at<int32_t>(ws, BL.fan_id);
+    uint32_t *fan_set = at<uint32_t>(ws, BL.fan_set);
+    uint2 *items = at<uint2>(ws, BL.fan_items);
+    const int64_t B = BL.num_sets;
+    const bool off = bc->abort != 0;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const int64_t per = ceil_div(B, (int64_t)blockDim.x);
+    const int64_t b0 = min((int64_t)threadIdx.x * per, B), b1 = min(b0 + per, B);
+    auto wants = [&](int64_t b) {
+        return !off && soct[b] >= kKgonMinS && !octs[b].abort && octs[b].has_edges && nonfin[b] == 0u;
+    };
+    uint32_t nf = 0, ni = 0;
+    for (int64_t b = b0; b < b1; ++b)
+        if (wants(b)) {
+            ++nf;
+            ni += (uint32_t)ceil_div((int64_t)sets[b].ntiles, (int64_t)kBxFanChunk);
+        }
+    uint32_t inf = nf, ini = ni;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, inf, o), c = __shfl_up_sync(0xffffffffu, ini, o);
+        if (lane >= (uint32_t)o) {
+            inf += a;
+            ini += c;
+        }
+    }
+    if (lane == 31) {
+        s_w[0][warp] = inf;
+        s_w[1][warp] = ini;
+    }
+    __syncthreads();
+    uint32_t bf = 0, bi = 0, tf = 0, ti = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+        if (w < warp) {
+            bf += s_w[0][w];
+            bi += s_w[1][w];
+        }
+        tf += s_w[0][w];
+        ti += s_w[1][w];
+    }
+    uint32_t f = bf + inf - nf, it = bi + ini - ni;
+    for (int64_t b = b0; b < b1; ++b) {
+        if (wants(b) && f < (uint32_t)BL.max_fan) {
+            fan_id[b] = (int32_t)f;
+            fan_set[f] = (uint32_t)b;
+            for (uint32_t c = 0; c < sets[b].ntiles; c += kBxFanChunk) items[it++] = make_uint2(f, sets[b].tile_base + c);
+            ++f;
+        } else {
+            fan_id[b] = -1;
+        }
+    }
+    if (threadIdx.x == 0) {
+        bc->nfan = min(tf, (uint32_t)BL.max_fan);
+        bc->nitems = min(ti, (uint32_t)BL.max_items);
+    }
+}
+
+// Per work item, every kBxBinStride-th tile (counted from the set's first):
+// each point's bin around the set's box centre, packed (r^2 bits << 32 |
+// ~index) into the fan's global slots by atomicMax (the read first saves
+// most atomics).
+__global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                         BatchLayout BL)
+{
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const Octagon *octs = at<Octagon>(ws, BL.octs);
+    const uint32_t *fan_set = at<uint32_t>(ws, BL.fan_set);
+    const uint2 *items = at<uint2>(ws, BL.fan_items);
+    unsigned long long *slots = at<unsigned long long>(ws, BL.fan_slot);
+    const uint32_t nitems = bc->nitems;
+    for (uint32_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const uint2 item = items[w];
+        const uint32_t b = fan_set[item.x];
+        const SetInfo &S = sets[b];
+        const float cx = octs[b].cx, cy = octs[b].cy;
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + S.pt_begin;
+        unsigned long long *sl = slots + (size_t)item.x * kFanBins;
+        const uint32_t tend = min(item.y + (uint32_t)kBxFanChunk, S.tile_base + S.ntiles);
+        for (uint32_t t = item.y; t < tend; ++t) {
+            if ((t - S.tile_base) % kBxBinStride) continue;
+            const int64_t lo = (int64_t)(t - S.tile_base) * kFiltTile, hi = min(lo + kFiltTile, S.n);
+            float2 p[FITEMS];
+#pragma unroll
+            for (int r = 0; r < FITEMS; ++r) {
+                const int64_t i = lo + r * FT + threadIdx.x;
+                p[r] = i < hi ? __ldg(p2 + i) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int r = 0; r < FITEMS; ++r) {
+                const int64_t i = lo + r * FT + threadIdx.x;
+                if (i < hi) {
+                    const float dx = p[r].x - cx, dy = p[r].y - cy;
+                    const int bin = fan_bin(dx, dy);
+                    const float r2 = __fmaf_rn(dx, dx, dy * dy);
+                    const unsigned long long v = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)~(uint32_t)i;
+                    if (v > __ldcg(sl + bin)) atomicMax(sl + bin, v);
+                }
+            }
+        }
+    }
+}
+
+// One block per fan (grid-stride): the exact centre check against the
+// set's octagon, then every bin's vertex (the sampled point of the last
+// non-empty bin at or before it, cyclically), and the slots are left zero
+// for the next call.  Thread t owns the kBinsPerThread consecutive bins
+// from t * kBinsPerThread: a scan in registers, one block scan of the
+// threads' last non-empty bins.
+constexpr int kBinsPerThread = kFanBins / BT;
+static_assert(kFanBins % BT == 0, "bins split evenly over the threads");
+
+__global__ void __launch_bounds__(BT) bx_fan_build_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                          BatchLayout BL)
+{
+    __shared__ int s_w[BT / 32];
+    __shared__ int s_ok;
+    const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const Octagon *octs = at<Octagon>(ws, BL.octs);
+    const uint32_t *fan_set = at<uint32_t>(ws, BL.fan_set);
+    uint32_t *fan_ok = at<uint32_t>(ws, BL.fan_ok);
+    float2 *fan_c = at<float2>(ws, BL.fan_c);
+    unsigned long long *slots = at<unsigned long long>(ws, BL.fan_slot);
+    float2 *verts = at<float2>(ws, BL.fan_v);
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t nfan = bc->nfan;
+    for (uint32_t k = blockIdx.x; k < nfan; k += gridDim.x) {
+        const uint32_t b = fan_set[k];
+        const Octagon &oct = octs[b];
+        const float cx = oct.cx, cy = oct.cy;
+        unsigned long long *sl = slots + (size_t)k * kFanBins + (size_t)tid * kBinsPerThread;
+        float2 *V = verts + (size_t)k * kFanBins + (size_t)tid * kBinsPerThread;
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin;
+        const int64_t nb = sets[b].n;
+        __syncthreads();   // shared words of the previous fan have been read
+        if (tid == 0) s_ok = 1;
+        __syncthreads();
+        if (tid < 8 && ((oct.valid >> tid) & 1u) && orient(oct.ax[tid], oct.ay[tid], oct.bx[tid], oct.by[tid], cx, cy) <= 0)
+            s_ok = 0;
+        // this thread's bins: the point index of each non-empty one, ~0u empty
+        uint32_t idx[kBinsPerThread];
+        int mylast = -1;
+#pragma unroll
+        for (int j = 0; j < kBinsPerThread; ++j) {
+            const unsigned long long v = __ldcg(sl + j);
+            idx[j] = v != 0ull ? ~(uint32_t)v : ~0u;
+            if (v != 0ull) mylast = j;
+        }
+        // the last non-empty bin of the threads before this one (exclusive
+        // max-scan over thread order), and the last overall (wrap-around)
+        int incl = mylast >= 0 ? (int)(tid * kBinsPerThread) + mylast : -1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl = max(incl, u);
+        }
+        int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = -1;
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        int before = -1, last = -1;
+        for (uint32_t w = 0; w < BT / 32; ++w) {
+            if (w < warp) before = max(before, s_w[w]);
+            last = max(last, s_w[w]);
+        }
+        before = max(before, excl);
+        const bool live = s_ok && last >= 0;
+        if (live) {
+            // the vertex index of a bin with no sample: that of the last
+            // non-empty bin before it (cyclically); it lies in another
+            // thread's range, read from the slots (not zeroed yet)
+            int cur = before >= 0 ? before : last;
+            uint32_t ci = ~(uint32_t)__ldcg(slots + (size_t)k * kFanBins + cur);
+#pragma unroll
+            for (int j = 0; j < kBinsPerThread; ++j) {
+                if (idx[j] != ~0u) ci = idx[j];
+                V[j] = __ldg(p2 + ((int64_t)ci < nb ? ci : 0u));
+            }
+        }
+        __syncthreads();   // every read of the slots is done
+#pragma unroll
+        for (int j = 0; j < kBinsPerThread; ++j) sl[j] = 0ull;
+        if (tid == 0) {
+            fan_ok[k] = live ? 1u : 0u;
+            fan_c[k] = make_float2(cx, cy);
+        }
+    }
+}
+
+// Persistent blocks take work items by ticket; the 28672 vertices of the
+// item's fan are loaded into shared memory when the fan changes (items of
+// one fan are consecutive).  The four groups of kFiltThreads threads share
+// the item's tiles; thread t holds the 16 keep bits of count-pass thread t
+// (point lo + r * 256 + t for bit r).  Kept points strictly inside the fan
+// lose their bit, and the tile's count drops by the number removed.
+__global__ void __launch_bounds__(CT, 1) bx_fan_refine_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                              BatchLayout BL)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sv = reinterpret_cast<float2 *>(smem_raw);   // kFanBins vertices
+    __shared__ uint32_t s_item;
+    BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
+    const SetInfo *sets = at<SetInfo>(ws, BL.sets);
+    const uint32_t *fan_set = at<uint32_t>(ws, BL.fan_set);
+    const uint32_t *fan_ok = at<uint32_t>(ws, BL.fan_ok);
+    const float2 *fan_c = at<float2>(ws, BL.fan_c);
+    const float2 *verts = at<float2>(ws, BL.fan_v);
+    const uint2 *items = at<uint2>(ws, BL.fan_items);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint32_t nitems = bc->nitems;
+    const uint32_t grp = threadIdx.x / kFiltThreads, t = threadIdx.x % kFiltThreads, lane = lane_id();
+    int64_t cur = -1;
+    for (;;) {
+        __syncthreads();   // s_item of the previous item has been read
+        if (threadIdx.x == 0) s_item = atomicAdd(&bc->fan_ticket, 1u);
+        __syncthreads();
+        const uint32_t w = s_item;
+        if (w >= nitems) break;
+        const uint2 item = items[w];
+        if (!fan_ok[item.x]) continue;   // block-uniform
+        if ((int64_t)item.x != cur) {
+            const float4 *src = reinterpret_cast<const float4 *>(verts + (size_t)item.x * kFanBins);
+            float4 *dst = reinterpret_cast<float4 *>(sv);
+            for (int i = threadIdx.x; i < kFanBins / 2; i += CT) dst[i] = __ldg(src + i);
+            __syncthreads();
+            cur = item.x;
+        }
+        const SetInfo &S = sets[fan_set[item.x]];
+        const float2 c = fan_c[item.x];
+        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + S.pt_begin;
+        const uint32_t tend = min(item.y + (uint32_t)kBxFanChunk, S.tile_base + S.ntiles);
+        for (uint32_t tile = item.y + grp; tile < tend; tile += CG) {
+            const int64_t lo = (int64_t)(tile - S.tile_base) * kFiltTile;
+            const uint32_t kb = bits[(size_t)tile * kFiltThreads + t];
+            uint32_t in = 0;
+            if (kb) {
+                float2 p[kFiltItems];
+#pragma unroll
+                for (int r = 0; r < kFiltItems; ++r)
+                    p[r] = ((kb >> r) & 1u) ? __ldcs(p2 + lo + r * kFiltThreads + t) : make_float2(0.0f, 0.0f);
+                uint32_t und = 0;
+#pragma unroll
+                for (int r = 0; r < kFiltItems; ++r) {
+                    const int f = fan_signs_f32(sv, c.x, c.y, p[r].x, p[r].y);
+                    in |= (f == 1 ? 1u : 0u) << r;
+                    und |= (f == 2 ? 1u : 0u) << r;
+                }
+                in &= kb;
+                und &= kb;
+                while (und) {
+                    const int r = __ffs(und) - 1;
+                    und &= und - 1u;
+                    const float2 q = p2[lo + r * kFiltThreads + t];
+                    if (fan_inside_exact(sv, c.x, c.y, q.x, q.y)) in |= 1u << r;
+                }
+                if (in) bits[(size_t)tile * kFiltThreads + t] = (uint16_t)(kb & ~in);
+            }
+            uint32_t removed = __popc(in);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) removed += __shfl_xor_sync(0xffffffffu, removed, o);
+            if (lane == 0 && removed) atomicAdd(&status[tile], 0ull - (unsigned long long)removed);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bx_fan(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
+{
+    const int sms = sm_count();
+    static const bool attrs = [] {
+        cudaFuncSetAttribute(bx_fan_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
+        return true;
+    }();
+    (void)attrs;
+    probe_before(CH_K_KGON, st);
+    bx_fan_select_kernel<<<1, 1024, 0, st>>>(ws, L, BL);
+    bx_fan_bins_kernel<<<(unsigned)(sms * 4), FT, 0, st>>>(pts, ws, L, BL);
+    bx_fan_build_kernel<<<(unsigned)(sms * 2), BT, 0, st>>>(pts, ws, L, BL);
+    bx_fan_refine_kernel<<<(unsigned)sms, CT, kFanSmem, st>>>(pts, ws, L, BL);
+    note_kernels(CH_K_KGON, 4);
+    probe_after(CH_K_KGON, st);
+    return cudaGetLastError();
+}
+
 }  // namespace ch

@@ -82,6 +82,9 @@ cudaError_t launch_bx_setup(const int64_t *offsets, void *ws, const Layout &L, c
                             int64_t n_cap, cudaStream_t st);
 cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
 cudaError_t launch_bx_filter(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
+// the fan test of the sets with many octagon survivors, on the batched
+// count pass's keep bits and tile counts (kgon.cu)
+cudaError_t launch_bx_fan(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
 cudaError_t launch_bx_sort(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
 cudaError_t launch_bx_chain(void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st);
 cudaError_t launch_bx_finish(void *ws, const Layout &L, const BatchLayout &BL, uint32_t *hull_idx,

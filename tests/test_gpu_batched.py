@@ -49,6 +49,21 @@ def test_mixed_sizes_and_distributions():
     check_batch(*concat(sets))
 
 
+def test_sets_with_the_fan_test():
+    # sets with at least 2^16 octagon survivors get the fan test: circle and
+    # displaced-circle sets from just above that size to several refine work
+    # items (64 tiles each), scaled and shifted, between small sets
+    rng = np.random.default_rng(11)
+    sets = []
+    for k, (dist, n) in enumerate([("circle", 1_000_003), ("normal", 300), ("displaced", 500_001),
+                                   ("circle", 70_000), ("displaced", 66_000), ("normal", 1_000_000),
+                                   ("circle", 262_145), ("displaced", 4095), ("circle", 65_536)]):
+        p = pointgen.make_points(dist, n, seed=500 + k).astype(np.float64)
+        p = p * rng.uniform(0.1, 10.0) + rng.uniform(-50, 50, 2)
+        sets.append(p.astype(np.float32))
+    check_batch(*concat(sets))
+
+
 def test_generated_batch_uneven_sizes():
     pts, offsets, _ = pointgen.make_batch(200, seed=7, min_n=100, max_n=200_000)
     check_batch(pts, offsets)
