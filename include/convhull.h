@@ -170,21 +170,26 @@ ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K
                        uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- launch tuning of ch_hull_batched ---------------------------------
- * Blocks per SM of the batched kernels' grids (results do not depend on
- * them: every such kernel walks tiles grid-stride or takes them by ticket).
+ * Launch shapes of the batched kernels; results do not depend on them
+ * (every such kernel walks tiles grid-stride, by ticket or over its own
+ * range, and the fan's vertices are input points whatever the sample).
  * 0 restores the built-in choice.  Process-wide (see "Host threads"
- * above), host-only; CH_ERR_ARG for
- * an unknown knob or a value outside 0..64.  The Python package's
- * autotuner sweeps these on a workload and caches the best in JSON. */
+ * above), host-only; CH_ERR_ARG for an unknown knob or a value outside the
+ * knob's range.  The Python package's autotuner sweeps these on a
+ * workload and caches the best in JSON. */
 typedef enum {
-    CH_TUNE_BX_EXTREMES = 0,    /* extremes sweep (default 8)                  */
-    CH_TUNE_BX_FILTER = 1,      /* filter count and scatter (default: occupancy) */
-    CH_TUNE_BX_SORT_PASS = 2,   /* radix-sort passes (default: occupancy)      */
-    CH_TUNE_BX_EMIT = 3,        /* chain compaction (default 4)                */
-    CH_TUNE_COUNT = 4
+    CH_TUNE_BX_EXTREMES = 0,    /* extremes sweep, blocks per SM 1..64 (default 8)          */
+    CH_TUNE_BX_FILTER = 1,      /* filter count and scatter, blocks per SM (default: occupancy) */
+    CH_TUNE_BX_SORT_PASS = 2,   /* radix-sort passes, blocks per SM (default: occupancy)     */
+    CH_TUNE_BX_EMIT = 3,        /* chain compaction, blocks per SM (default 4)              */
+    CH_TUNE_BX_FAN_STRIDE = 4,  /* the fan's bins sample every k-th tile of a set, 1..64 (default 2) */
+    CH_TUNE_BX_FAN_CHUNK = 5,   /* tiles per work item of the fan refine: 8, 16, 32 or 64 (default 64) */
+    CH_TUNE_BX_EXT_ITEMS = 6,   /* points per thread per 4096-point tile of the extremes sweep:
+                                   4, 8 or 16, i.e. blocks of 1024, 512 or 256 threads (default 16) */
+    CH_TUNE_COUNT = 7
 } ch_tune_knob;
-ch_status ch_tune_set(int32_t knob, int32_t blocks_per_sm);
-ch_status ch_tune_get(int32_t knob, int32_t *blocks_per_sm);
+ch_status ch_tune_set(int32_t knob, int32_t value);
+ch_status ch_tune_get(int32_t knob, int32_t *value);
 
 /* ---- learned proposal of the K-direction polygon (not in the paper: its
  * extension to more directions, picked per point set) ---------------------

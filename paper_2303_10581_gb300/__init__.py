@@ -35,7 +35,7 @@ SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter",
            "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
            "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
            "ch_tune_set", "ch_tune_get")
-TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit")
+TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit", "bx_fan_stride", "bx_fan_chunk", "bx_ext_items")
 # ch_filter_noalloc reports a device-side error as this bit | the status code in its count
 NOALLOC_FAILED = 0x80000000
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")

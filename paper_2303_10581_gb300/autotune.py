@@ -1,7 +1,8 @@
-"""Autotuner of ch_hull_batched's launch grids.
+"""Autotuner of ch_hull_batched's launch shapes.
 
-A coordinate search over the blocks-per-SM knobs (``ch_tune_set``) on a
-given batch, timing the batched call with CUDA events; the best setting is
+A coordinate search over the launch knobs (``ch_tune_set``: blocks per SM
+of four kernels, the tile sampling and work-item size of the fan, the
+points per thread and block size of the extremes sweep) on a given batch, timing the batched call with CUDA events; the best setting is
 cached in a JSON file keyed by the GPU and the batch's shape (sets and
 points, rounded to powers of two) and applied with ``apply``.  Results of
 the call do not depend on the knobs, only its speed.
@@ -15,10 +16,13 @@ import os
 from . import TUNE_KNOBS, ch_hull_batched, ch_tune_get, ch_tune_set
 
 CANDIDATES = {
-    "bx_extremes": (2, 4, 8, 16),
+    "bx_extremes": (2, 4, 8, 16),      # blocks per SM
     "bx_filter": (2, 4, 6, 8),
     "bx_sort_pass": (1, 2, 3),
     "bx_emit": (1, 2, 4, 8),
+    "bx_fan_stride": (1, 2, 4),        # the fan's bins sample every k-th tile
+    "bx_fan_chunk": (16, 32, 64),      # tiles per work item of the fan refine
+    "bx_ext_items": (4, 8, 16),        # points per thread per tile (block of 1024, 512, 256 threads)
 }
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "convhull_gb300", "tune.json")
 

@@ -42,17 +42,20 @@ int tune_value(int knob)
 }
 }  // namespace ch
 
-extern "C" ch_status ch_tune_set(int32_t knob, int32_t blocks_per_sm)
+extern "C" ch_status ch_tune_set(int32_t knob, int32_t value)
 {
-    if (knob < 0 || knob >= CH_TUNE_COUNT || blocks_per_sm < 0 || blocks_per_sm > 64) return CH_ERR_ARG;
-    ch::g_tune[knob].store(blocks_per_sm, std::memory_order_relaxed);
+    if (knob < 0 || knob >= CH_TUNE_COUNT || value < 0 || value > 64) return CH_ERR_ARG;
+    if (knob == CH_TUNE_BX_FAN_CHUNK && value && value != 8 && value != 16 && value != 32 && value != 64)
+        return CH_ERR_ARG;
+    if (knob == CH_TUNE_BX_EXT_ITEMS && value && value != 4 && value != 8 && value != 16) return CH_ERR_ARG;
+    ch::g_tune[knob].store(value, std::memory_order_relaxed);
     return CH_OK;
 }
 
-extern "C" ch_status ch_tune_get(int32_t knob, int32_t *blocks_per_sm)
+extern "C" ch_status ch_tune_get(int32_t knob, int32_t *value)
 {
-    if (knob < 0 || knob >= CH_TUNE_COUNT || !blocks_per_sm) return CH_ERR_ARG;
-    *blocks_per_sm = ch::g_tune[knob].load(std::memory_order_relaxed);
+    if (knob < 0 || knob >= CH_TUNE_COUNT || !value) return CH_ERR_ARG;
+    *value = ch::g_tune[knob].load(std::memory_order_relaxed);
     return CH_OK;
 }
 

@@ -242,7 +242,8 @@ struct BatchCtrl {
     uint32_t fan_ticket;  // next work item of the fan refine
     uint32_t pad;
 };
-constexpr int kBxFanChunk = 64;       // tiles per work item of the batched fan refine
+constexpr int kBxFanChunk = 64;       // tiles per work item of the batched fan refine (built-in)
+constexpr int kBxFanChunkMin = 8;     // the smallest tunable one (sizes the work-item list)
 
 // Extra workspace of ch_hull_batched, after the single-set regions.
 struct BatchLayout {
@@ -356,7 +357,7 @@ __host__ __device__ inline BatchLayout make_batch_layout(const Layout &L, int64_
     B.lower = L.keys[1];   // the second sort buffer is free once the sort ends in buffer 0
     // a set with a fan has at least 2^16 points
     B.max_fan = sets < L.n / 65536 + 1 ? sets : L.n / 65536 + 1;
-    B.max_items = B.tiles_max / kBxFanChunk + B.max_fan + 1;
+    B.max_items = B.tiles_max / kBxFanChunkMin + B.max_fan + 1;
     B.fan_id = take((size_t)sets * 4);
     B.fan_set = take((size_t)B.max_fan * 4);
     B.fan_ok = take((size_t)B.max_fan * 4);

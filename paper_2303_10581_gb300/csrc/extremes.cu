@@ -743,8 +743,9 @@ __global__ void octagon_kernel(const float *__restrict__ pts, int64_t n, const u
 // folded into the set's slots whenever the range moves on to another set
 // (sets are contiguous in tile order, so a block flushes once per set it
 // touches).
+template <int NWARP>
 __device__ __forceinline__ void bx_flush(Best &best, float &nf, int64_t b, unsigned long long *slots,
-                                         uint32_t *nonfin, float (&sk)[8][8], uint32_t (&si)[8][8], int &s_bad)
+                                         uint32_t *nonfin, float (&sk)[NWARP][8], uint32_t (&si)[NWARP][8], int &s_bad)
 {
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
 #pragma unroll
@@ -770,7 +771,7 @@ __device__ __forceinline__ void bx_flush(Best &best, float &nf, int64_t b, unsig
     if (warp == 0 && lane < 8) {
         float k = sk[0][lane];
         uint32_t i = si[0][lane];
-        for (int w = 1; w < 8; ++w) combine(k, i, sk[w][lane], si[w][lane]);
+        for (int w = 1; w < NWARP; ++w) combine(k, i, sk[w][lane], si[w][lane]);
         if (i != 0xffffffffu)
             atomicMax(&slots[(size_t)b * 8 + lane], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
         if (lane == 0 && s_bad) atomicOr(&nonfin[b], 1u);
@@ -783,8 +784,9 @@ __device__ __forceinline__ void bx_flush(Best &best, float &nf, int64_t b, unsig
     nf = 0.0f;
 }
 
-__global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restrict__ pts, void *ws, Layout L,
-                                                          BatchLayout BL)
+template <int T>   // threads per block: each holds kFiltTile / T points of a tile
+__global__ void __launch_bounds__(T) bx_extremes_kernel(const float *__restrict__ pts, void *ws, Layout L,
+                                                        BatchLayout BL)
 {
     const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
     if (bc->abort) return;
@@ -792,13 +794,13 @@ __global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restric
     const uint32_t *tile_set = at<uint32_t>(ws, BL.tile_set);
     unsigned long long *slots = at<unsigned long long>(ws, BL.ext_slot);
     uint32_t *nonfin = at<uint32_t>(ws, BL.nonfinite);
-    __shared__ float sk[8][8];
-    __shared__ uint32_t si_[8][8];
+    __shared__ float sk[T / 32][8];
+    __shared__ uint32_t si_[T / 32][8];
     __shared__ int s_bad;
-    const int64_t T = bc->tiles;
-    const int64_t per = ceil_div(T, (int64_t)gridDim.x);
-    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
-    constexpr int R = kFiltTile / 256;   // points per thread per tile
+    const int64_t NT = bc->tiles;
+    const int64_t per = ceil_div(NT, (int64_t)gridDim.x);
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(NT, t0 + per);
+    constexpr int R = kFiltTile / T;   // points per thread per tile
     Best best;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -828,12 +830,12 @@ __global__ void __launch_bounds__(256) bx_extremes_kernel(const float *__restric
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t i = lo + r * 256 + threadIdx.x;
+            const int64_t i = lo + r * T + threadIdx.x;
             v[r] = i < hi ? __ldcs(p2 + i) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int64_t i = lo + r * 256 + threadIdx.x;
+            const int64_t i = lo + r * T + threadIdx.x;
             if (i < hi) {
                 nf = __fmaf_rn(v[r].x, 0.0f, __fmaf_rn(v[r].y, 0.0f, nf));
                 consider(best, v[r].x, v[r].y, (uint32_t)i);
@@ -875,9 +877,13 @@ __global__ void __launch_bounds__(256) bx_octagon_kernel(const float *__restrict
 cudaError_t launch_bx_extremes(const float *pts, void *ws, const Layout &L, const BatchLayout &BL, cudaStream_t st)
 {
     const int per_sm = tune_value(CH_TUNE_BX_EXTREMES) ? tune_value(CH_TUNE_BX_EXTREMES) : 8;
+    const int items = tune_value(CH_TUNE_BX_EXT_ITEMS) ? tune_value(CH_TUNE_BX_EXT_ITEMS) : 16;
     int64_t blocks = std::min<int64_t>(BL.tiles_max, (int64_t)sm_count() * per_sm);
+    const unsigned g = (unsigned)std::max<int64_t>(blocks, 1);
     probe_before(CH_K_EXTREMES, st);
-    bx_extremes_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(pts, ws, L, BL);
+    if (items == 4) bx_extremes_kernel<1024><<<g, 1024, 0, st>>>(pts, ws, L, BL);
+    else if (items == 8) bx_extremes_kernel<512><<<g, 512, 0, st>>>(pts, ws, L, BL);
+    else bx_extremes_kernel<256><<<g, 256, 0, st>>>(pts, ws, L, BL);
     bx_octagon_kernel<<<(unsigned)ceil_div(BL.num_sets, 8), 256, 0, st>>>(pts, ws, L, BL);
     note_kernels(CH_K_EXTREMES, 2);
     probe_after(CH_K_EXTREMES, st);

@@ -467,11 +467,11 @@ namespace {
 // many sets (ch_hull_batched): the same fan for every set with at least
 // kKgonMinS octagon survivors, between the batched count pass and its scan
 // ---------------------------------------------------------------------------
-constexpr int kBxBinStride = 2;   // the bins see every 2nd tile of a set (1 and 4 measured slower overall)
+constexpr int kBxBinStride = 2;   // built-in: the bins see every 2nd tile of a set (1 and 4 measured slower overall)
 
 // One block: numbers the sets that get a fan and lays out the refine's
 // work items (runs of up to kBxFanChunk tiles of one such set).
-__global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L, BatchLayout BL)
+__global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L, BatchLayout BL, uint32_t chunk)
 {
     __shared__ uint32_t s_w[2][32];
     BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L,
     for (int64_t b = b0; b < b1; ++b)
         if (wants(b)) {
             ++nf;
-            ni += (uint32_t)ceil_div((int64_t)sets[b].ntiles, (int64_t)kBxFanChunk);
+            ni += (uint32_t)ceil_div((int64_t)sets[b].ntiles, (int64_t)chunk);
         }
     uint32_t inf = nf, ini = ni;
 #pragma unroll
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L,
         if (wants(b) && f < (uint32_t)BL.max_fan) {
             fan_id[b] = (int32_t)f;
             fan_set[f] = (uint32_t)b;
-            for (uint32_t c = 0; c < sets[b].ntiles; c += kBxFanChunk) items[it++] = make_uint2(f, sets[b].tile_base + c);
+            for (uint32_t c = 0; c < sets[b].ntiles; c += chunk) items[it++] = make_uint2(f, sets[b].tile_base + c);
             ++f;
         } else {
             fan_id[b] = -1;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L,
 // ~index) into the fan's global slots by atomicMax (the read first saves
 // most atomics).
 __global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict__ pts, void *ws, Layout L,
-                                                         BatchLayout BL)
+                                                         BatchLayout BL, uint32_t chunk, uint32_t stride)
 {
     const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
     const SetInfo *sets = at<SetInfo>(ws, BL.sets);
@@ -557,9 +557,9 @@ __global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict
         const float cx = octs[b].cx, cy = octs[b].cy;
         const float2 *p2 = reinterpret_cast<const float2 *>(pts) + S.pt_begin;
         unsigned long long *sl = slots + (size_t)item.x * kFanBins;
-        const uint32_t tend = min(item.y + (uint32_t)kBxFanChunk, S.tile_base + S.ntiles);
+        const uint32_t tend = min(item.y + chunk, S.tile_base + S.ntiles);
         for (uint32_t t = item.y; t < tend; ++t) {
-            if ((t - S.tile_base) % kBxBinStride) continue;
+            if ((t - S.tile_base) % stride) continue;
             const int64_t lo = (int64_t)(t - S.tile_base) * kFiltTile, hi = min(lo + kFiltTile, S.n);
             float2 p[FITEMS];
 #pragma unroll
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(BT) bx_fan_build_kernel(const float *__restric
 // (point lo + r * 256 + t for bit r).  Kept points strictly inside the fan
 // lose their bit, and the tile's count drops by the number removed.
 __global__ void __launch_bounds__(CT, 1) bx_fan_refine_kernel(const float *__restrict__ pts, void *ws, Layout L,
-                                                              BatchLayout BL)
+                                                              BatchLayout BL, uint32_t chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sv = reinterpret_cast<float2 *>(smem_raw);   // kFanBins vertices
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(CT, 1) bx_fan_refine_kernel(const float *__res
         const SetInfo &S = sets[fan_set[item.x]];
         const float2 c = fan_c[item.x];
         const float2 *p2 = reinterpret_cast<const float2 *>(pts) + S.pt_begin;
-        const uint32_t tend = min(item.y + (uint32_t)kBxFanChunk, S.tile_base + S.ntiles);
+        const uint32_t tend = min(item.y + chunk, S.tile_base + S.ntiles);
         for (uint32_t tile = item.y + grp; tile < tend; tile += CG) {
             const int64_t lo = (int64_t)(tile - S.tile_base) * kFiltTile;
             const uint32_t kb = bits[(size_t)tile * kFiltThreads + t];
@@ -756,11 +756,14 @@ cudaError_t launch_bx_fan(const float *pts, void *ws, const Layout &L, const Bat
         return true;
     }();
     (void)attrs;
+    const uint32_t chunk = tune_value(CH_TUNE_BX_FAN_CHUNK) ? (uint32_t)tune_value(CH_TUNE_BX_FAN_CHUNK) : kBxFanChunk;
+    const uint32_t stride = tune_value(CH_TUNE_BX_FAN_STRIDE) ? (uint32_t)tune_value(CH_TUNE_BX_FAN_STRIDE)
+                                                              : kBxBinStride;
     probe_before(CH_K_KGON, st);
-    bx_fan_select_kernel<<<1, 1024, 0, st>>>(ws, L, BL);
-    bx_fan_bins_kernel<<<(unsigned)(sms * 4), FT, 0, st>>>(pts, ws, L, BL);
+    bx_fan_select_kernel<<<1, 1024, 0, st>>>(ws, L, BL, chunk);
+    bx_fan_bins_kernel<<<(unsigned)(sms * 4), FT, 0, st>>>(pts, ws, L, BL, chunk, stride);
     bx_fan_build_kernel<<<(unsigned)(sms * 2), BT, 0, st>>>(pts, ws, L, BL);
-    bx_fan_refine_kernel<<<(unsigned)sms, CT, kFanSmem, st>>>(pts, ws, L, BL);
+    bx_fan_refine_kernel<<<(unsigned)sms, CT, kFanSmem, st>>>(pts, ws, L, BL, chunk);
     note_kernels(CH_K_KGON, 4);
     probe_after(CH_K_KGON, st);
     return cudaGetLastError();

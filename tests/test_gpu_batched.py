@@ -202,15 +202,26 @@ def test_cuda_graph_replay():
             assert np.array_equal(got[h[b]:h[b + 1]], want), (seed, b)
 
 
-@pytest.mark.parametrize("per_sm", [1, 3, 16])
-def test_launch_grids_do_not_change_results(per_sm):
-    """Every batched kernel walks tiles grid-stride or by ticket: any grid
-    gives the same hulls."""
+GRID_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit")
+
+
+@pytest.mark.parametrize("per_sm,stride,chunk,items", [(1, 1, 8, 4), (3, 3, 16, 8), (16, 4, 64, 16)])
+def test_launch_shapes_do_not_change_results(per_sm, stride, chunk, items):
+    """Every batched kernel walks tiles grid-stride, by ticket or over its
+    own range, and the fan's vertices are input points whatever tiles the
+    bins sample: any grid, sampling stride, work-item size and points per
+    thread give the same hulls (the batch has sets with the fan)."""
     pts, offsets, _ = pointgen.make_batch(300, seed=41, min_n=50, max_n=300_000)
+    extra = pointgen.make_points("circle", 400_000, seed=42)   # several fan work items
+    pts = np.concatenate([pts, extra])
+    offsets = np.concatenate([offsets, [offsets[-1] + len(extra)]])
     try:
-        for k in ch.TUNE_KNOBS:
+        for k in GRID_KNOBS:
             ch.ch_tune_set(k, per_sm)
-        check_batch(pts, offsets, sample=range(0, 300, 7))
+        ch.ch_tune_set("bx_fan_stride", stride)
+        ch.ch_tune_set("bx_fan_chunk", chunk)
+        ch.ch_tune_set("bx_ext_items", items)
+        check_batch(pts, offsets, sample=list(range(0, 300, 7)) + [300])
     finally:
         for k in ch.TUNE_KNOBS:
             ch.ch_tune_set(k, 0)
