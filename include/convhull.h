@@ -169,6 +169,36 @@ ch_status ch_filter_kgon(const float *pts, int64_t n, const float *dirs, int32_t
 ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *hull_idx,
                        uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
 
+/* ch_hull with a second filter polygon between the octagon and the hull
+ * step (the paper's Sec. 3.1 idea with K directions, applied to what the
+ * octagon leaves): after the octagon's count pass, vertex k of the K-gon
+ * is the survivor with the largest key fl(fl(c_k x) + fl(s_k y)) (dirs as
+ * in ch_filter_kgon; lowest index on ties), and survivors strictly left of
+ * every edge of non-zero length of that vertex sequence are dropped too;
+ * then the fan test, sort and chain of ch_hull.  K in {8, 16, 32, 64};
+ * K = 8 adds no polygon (ch_hull exactly; dirs may be NULL).  The hull is
+ * ch_hull's.  ext_out (device, K entries, may be NULL) receives the K-gon's
+ * vertex indices when the second polygon ran: not when the speculative
+ * sweep served the filter (ch_hull_counts) or the single-pass schedule is
+ * set, which leave no keep bits to refine.  Errors as ch_hull and
+ * ch_filter_kgon. */
+ch_status ch_hull_octagon_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *ext_out,
+                               uint32_t *hull_idx, uint32_t *hull_count, void *ws, size_t ws_bytes,
+                               void *stream);
+
+/* The learned proposal end to end without a host synchronisation (not in
+ * the paper): the features (ch_kgon_features) and the MLP (ch_mlp_forward)
+ * of the set, then on the device K from the arg-max of the four K-logits
+ * and the directions at angles 2 pi k / K + offset_k pi / K (offsets
+ * clipped to +-0.45; cos and sin in binary64, rounded once; a multiple of
+ * pi / 4 with zero offset takes the octagon's integer direction), then
+ * ch_hull_octagon_kgon with that polygon (K = 8: ch_hull).  params: device,
+ * the MLP's BF16 parameters (ch_mlp_forward).  dirs_out (device, 128
+ * floats, may be NULL) and k_out (device, may be NULL) receive the choice.
+ * The hull is ch_hull's whatever the MLP outputs. */
+ch_status ch_hull_learned(const float *pts, int64_t n, const void *params, float *dirs_out, int32_t *k_out,
+                          uint32_t *hull_idx, uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);
+
 /* ---- launch tuning of ch_hull_batched ---------------------------------
  * Launch shapes of the batched kernels; results do not depend on them
  * (every such kernel walks tiles grid-stride, by ticket or over its own

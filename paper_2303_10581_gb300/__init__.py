@@ -34,7 +34,7 @@ SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter",
            "ch_hull_batched", "ch_last_error", "ch_probe_start", "ch_probe_stop", "ch_filter_noalloc",
            "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
            "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
-           "ch_tune_set", "ch_tune_get")
+           "ch_tune_set", "ch_tune_get", "ch_hull_octagon_kgon", "ch_hull_learned")
 TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit", "bx_fan_stride", "bx_fan_chunk", "bx_ext_items")
 # ch_filter_noalloc reports a device-side error as this bit | the status code in its count
 NOALLOC_FAILED = 0x80000000
@@ -79,6 +79,8 @@ def load(build_if_missing: bool = True):
     lib.ch_probe_stop.argtypes = [p, p]
     lib.ch_filter_noalloc.argtypes = [p, i64, p, p, p, p, p]
     lib.ch_filter_variant.argtypes = [ctypes.c_int32]
+    lib.ch_hull_octagon_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, p, sz, p]
+    lib.ch_hull_learned.argtypes = [p, i64, p, p, p, p, p, p, sz, p]
     lib.ch_hull_counts.argtypes = [p, sz, i64, p, p]
     lib.ch_filter_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, p, p, sz, p]
     lib.ch_hull_kgon.argtypes = [p, i64, p, ctypes.c_int32, p, p, p, sz, p]
@@ -180,6 +182,18 @@ def ch_hull_kgon(pts, dirs, hull_idx, hull_count, ws, stream=None):
     _check(load().ch_hull_kgon(_ptr(pts, "pts"), pts.shape[0], _ptr(dirs, "dirs"), dirs.shape[0],
                                _ptr(hull_idx, "hull_idx"), _ptr(hull_count, "hull_count"), _ptr(ws, "ws"),
                                ws.numel(), _stream(stream)), "ch_hull_kgon")
+
+
+def ch_hull_octagon_kgon(pts, dirs, K, ext_out, hull_idx, hull_count, ws, stream=None):
+    _check(load().ch_hull_octagon_kgon(_ptr(pts, "pts"), pts.shape[0], _ptr(dirs, "dirs"), int(K), _ptr(ext_out, "ext_out"),
+                                       _ptr(hull_idx, "hull_idx"), _ptr(hull_count, "hull_count"), _ptr(ws, "ws"),
+                                       ws.numel(), _stream(stream)), "ch_hull_octagon_kgon")
+
+
+def ch_hull_learned(pts, params, dirs_out, k_out, hull_idx, hull_count, ws, stream=None):
+    _check(load().ch_hull_learned(_ptr(pts, "pts"), pts.shape[0], _ptr(params, "params"), _ptr(dirs_out, "dirs_out"),
+                                  _ptr(k_out, "k_out"), _ptr(hull_idx, "hull_idx"), _ptr(hull_count, "hull_count"),
+                                  _ptr(ws, "ws"), ws.numel(), _stream(stream)), "ch_hull_learned")
 
 
 def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):

@@ -178,6 +178,25 @@ extern "C" ch_status ch_hull_kgon(const float *pts, int64_t n, const float *dirs
     return cuda_status(e);
 }
 
+namespace {
+
+// ch_hull's launches with an optional second polygon between the octagon's
+// count pass and the fan
+cudaError_t hull_pipeline(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
+                          const Layout &L, const KgonStage *kg, cudaStream_t st)
+{
+    const int variant = filter_variant();
+    cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
+                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0);
+    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true, true, kg);
+    if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
+    if (e == cudaSuccess) e = launch_sort(ws, L, st);
+    if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
+    return e;
+}
+
+}  // namespace
+
 extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
                              size_t ws_bytes, void *stream)
 {
@@ -189,13 +208,47 @@ extern "C" ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, ui
     const Layout L = make_layout(n);
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
     // the two-pass schedule takes the speculative sweep's candidates
-    const int variant = filter_variant();
-    cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
-                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0);
-    if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true);
-    if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
-    if (e == cudaSuccess) e = launch_sort(ws, L, st);
-    if (e == cudaSuccess) e = launch_chain(ws, L, hull_idx, hull_count, st);
+    return cuda_status(hull_pipeline(pts, n, hull_idx, hull_count, ws, L, nullptr, st));
+}
+
+
+extern "C" ch_status ch_hull_octagon_kgon(const float *pts, int64_t n, const float *dirs, int32_t K, uint32_t *ext_out,
+                                          uint32_t *hull_idx, uint32_t *hull_count, void *ws, size_t ws_bytes,
+                                          void *stream)
+{
+    if (!hull_count || n < 0 || !aligned(hull_count, 4) || !kgon_k_ok(K)) return CH_ERR_ARG;
+    if (n >= kMaxHullN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(hull_count, 0, sizeof(uint32_t), st));
+    if (!pts || !hull_idx || !aligned(pts, 8) || !aligned(hull_idx, 4) || (K != 8 && (!dirs || !aligned(dirs, 4))) ||
+        (ext_out && !aligned(ext_out, 4)))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    const KgonStage kg{dirs, nullptr, K, ext_out};
+    return cuda_status(hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st));
+}
+
+extern "C" ch_status ch_hull_learned(const float *pts, int64_t n, const void *params, float *dirs_out, int32_t *k_out,
+                                     uint32_t *hull_idx, uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!hull_count || n < 0 || !aligned(hull_count, 4)) return CH_ERR_ARG;
+    if (n >= kMaxHullN) return CH_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(hull_count, 0, sizeof(uint32_t), st));
+    if (!pts || !params || !hull_idx || !aligned(pts, 8) || !aligned(params, 4) || !aligned(hull_idx, 4) ||
+        (dirs_out && !aligned(dirs_out, 4)) || (k_out && !aligned(k_out, 4)))
+        return CH_ERR_ARG;
+    const Layout L = make_layout(n);
+    if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    LearnScratch *ls = at<LearnScratch>(ws, L.learn);
+    if (ch_status s = ch_kgon_features(pts, n, ls->feat, stream)) return s;
+    if (ch_status s = ch_mlp_forward(ls->feat, 1, params, ls->h1, ls->h2, ls->out, stream)) return s;
+    cudaError_t e = launch_kx_choose(ls->out, &ls->K, ls->dirs, st);
+    const KgonStage kg{ls->dirs, &ls->K, 0, nullptr};
+    if (e == cudaSuccess) e = hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st);
+    if (e == cudaSuccess && dirs_out) e = cudaMemcpyAsync(dirs_out, ls->dirs, sizeof(ls->dirs), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, &ls->K, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     return cuda_status(e);
 }
 

@@ -166,6 +166,17 @@ struct SpecCtrl {
     uint32_t skept[kSpecMaxSeg];          // survivors of the octagon per segment (their slots in utmp)
 };
 
+// ch_hull_learned: features, activations and outputs of the MLP, and the
+// polygon it picks (K and the directions)
+struct LearnScratch {
+    float feat[1024];
+    float h1[64], h2[64];
+    float out[68];
+    float dirs[2 * kMaxDirs];
+    int32_t K;
+    int32_t pad[3];
+};
+
 // persistent words: survive calls, cleared by ch_last_error
 struct Persist {
     uint32_t error;
@@ -195,6 +206,7 @@ struct Layout {
     size_t kgon;            // Kgon
     size_t utmp;          // u32[n]
     size_t spec, p0;        // SpecCtrl, the speculative sweep's test region (SpecBox, extremes.cu)
+    size_t learn;           // the learned proposal's scratch (LearnScratch)
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
 };
@@ -326,6 +338,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.utmp = take((size_t)n * 4);
     L.spec = take(sizeof(SpecCtrl));
     L.p0 = take(256);
+    L.learn = take(sizeof(LearnScratch));
     L.total = o;
     return L;
 }

@@ -986,7 +986,7 @@ cudaError_t launch_single(const float *pts, int64_t n, void *ws, const Layout &L
 // candidates (Octagon::spec)
 template <int G, bool KEYS, bool BOX>
 cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
-                            float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan)
+                            float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan, const KgonStage *kg)
 {
     static int per_sm_c = occupancy(filter_count_kernel<G, BOX>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
@@ -994,6 +994,12 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     const int64_t bc = std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
     filter_count_kernel<G, BOX><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    if (kg && (kg->kdev || kg->K != 8)) {   // the second polygon, over the octagon's survivors
+        probe_after(CH_K_FILTER, st);
+        const cudaError_t e = launch_kx_sv(pts, n, kg->dirs, kg->kdev, kg->K, kg->ext_out, ws, L, bc, st);
+        if (e != cudaSuccess) return e;
+        probe_before(CH_K_FILTER, st);
+    }
     if (fan) {   // timed as its own group, between the filter's two
         probe_after(CH_K_FILTER, st);
         const cudaError_t e = launch_fan(pts, n, G == 2, bc, ws, L, st);
@@ -1014,14 +1020,14 @@ std::atomic<int> g_filter_variant{0};
 template <int G, bool KEYS>
 cudaError_t launch_variant(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                            float *surv_pts, uint32_t *surv_count, cudaStream_t st, int variant, bool fan,
-                           bool data_extremes)
+                           bool data_extremes, const KgonStage *kg)
 {
     probe_before(CH_K_FILTER, st);
     cudaError_t e;
     if (variant == 1) e = launch_single<G, KEYS>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st);
     else if (KEYS || data_extremes)
-        e = launch_two_pass<G, KEYS, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
-    else e = launch_two_pass<G, false, true>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan);
+        e = launch_two_pass<G, KEYS, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan, kg);
+    else e = launch_two_pass<G, false, true>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, fan, nullptr);
     probe_after(CH_K_FILTER, st);
     return e;
 }
@@ -1032,15 +1038,17 @@ int filter_variant() { return g_filter_variant.load(std::memory_order_relaxed); 
 
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st, int variant,
-                          bool fan, bool data_extremes)
+                          bool fan, bool data_extremes, const KgonStage *kg)
 {
     const int v = variant < 0 ? g_filter_variant.load(std::memory_order_relaxed) : variant;
     const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
     if (keys_mode)
-        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true)
-                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true);
-    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes)
-               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes);
+        return vec ? launch_variant<2, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true, kg)
+                   : launch_variant<1, true>(pts, n, ws, L, nullptr, nullptr, nullptr, st, v, fan, true, kg);
+    return vec ? launch_variant<2, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes,
+                                          nullptr)
+               : launch_variant<1, false>(pts, n, ws, L, surv_idx, surv_pts, surv_count, st, v, false, data_extremes,
+                                          nullptr);
 }
 
 cudaError_t launch_filter_scatter(const float *pts, int64_t n, int64_t grid, void *ws, const Layout &L,

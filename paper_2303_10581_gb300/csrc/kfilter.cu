@@ -374,6 +374,230 @@ __global__ void __launch_bounds__(kFiltThreads) kx_count_kernel(const float *__r
     if (t == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = block_total;
 }
 
+
+// ---------------------------------------------------------------------------
+// A K-direction polygon over the octagon's survivors (ch_hull_octagon_kgon,
+// ch_hull_learned).  After the octagon's count pass, the vertex of
+// direction k is the survivor with the largest key fl(fl(c_k x) + fl(s_k y)),
+// lowest index on ties, and every survivor strictly left of every edge of
+// non-zero length of that vertex sequence is dropped too.  Both polygons
+// have input points as vertices, so what is dropped is strictly inside the
+// hull (Sec. 3.2's argument, twice); a point survives when it is strictly
+// inside neither.  The extremes of every direction survive the octagon
+// (they lie on the hull's boundary), so up to rounding of the keys these
+// are the polygon's vertices over all points; the survivors' extremes are
+// what is computed.
+// ---------------------------------------------------------------------------
+constexpr int ST = 256;   // threads per block of the survivors' passes (one per count-pass thread)
+
+// Whether the K-gon stage runs in this call: not aborted, the octagon's
+// count pass left keep bits (no speculative sweep), and K is the stage's
+// (kdev: the device's choice, when the host did not fix it).
+__device__ __forceinline__ bool kx_stage_on(const Octagon *oct, const int32_t *kdev, int K)
+{
+    return !oct->abort && !oct->spec && (kdev == nullptr || *kdev == K);
+}
+
+template <int G>
+__device__ __forceinline__ int64_t sv_point(int64_t base, uint32_t t, int q)
+{
+    return base + (int64_t)((q / G) * kFiltThreads + t) * G + q % G;
+}
+
+// Survivors of each tile are staged in shared memory (compacted), then
+// thread t keeps the best of direction t mod K over its share of them.
+template <int K, int G>
+__global__ void __launch_bounds__(ST) kx_sv_extremes_kernel(const float *__restrict__ pts, int64_t n,
+                                                            const float *__restrict__ dirs, const int32_t *kdev,
+                                                            uint32_t *ext_out, void *ws, Layout L)
+{
+    static_assert(K >= 8 && K <= kMaxDirs && ST % K == 0 && ST == kFiltThreads, "directions split the block evenly");
+    constexpr int PARTS = ST / K;
+    __shared__ float2 s_p[kFiltTile];
+    __shared__ uint16_t s_i[kFiltTile];   // index - base
+    __shared__ uint32_t s_w[ST / 32];
+    __shared__ uint32_t s_total;
+    __shared__ float s_bk[ST];
+    __shared__ uint32_t s_bi[ST];
+    __shared__ uint32_t s_ext[kMaxDirs];
+    __shared__ int s_last;
+    Octagon *oct = at<Octagon>(ws, L.oct);
+    if (!kx_stage_on(oct, kdev, K)) return;
+    KxCtrl *kc = at<KxCtrl>(ws, L.kxctrl);
+    const uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    const float2 *p2 = reinterpret_cast<const float2 *>(pts);
+    const uint32_t t = threadIdx.x, warp = t >> 5, lane = lane_id();
+    const int d = (int)t % K, part = (int)t / K;
+    const float c = dirs[2 * d], sn = dirs[2 * d + 1];
+    float best = __int_as_float(0x7fc00000);   // NaN: no candidate yet
+    uint32_t bi = 0xffffffffu;
+    const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * kFiltTile;
+        const uint32_t kb = bits[tile * kFiltThreads + t];
+        const uint32_t cnt = __popc(kb);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint32_t off = incl - cnt, total = 0;
+#pragma unroll
+        for (int w = 0; w < ST / 32; ++w) {
+            if (w < (int)warp) off += s_w[w];
+            total += s_w[w];
+        }
+        if (total == 0u) {   // block-uniform
+            __syncthreads();
+            continue;
+        }
+        for (uint32_t b = kb; b; b &= b - 1u) {
+            const int q = __ffs(b) - 1;
+            const int64_t i = sv_point<G>(base, t, q);
+            s_p[off] = p2[i];
+            s_i[off] = (uint16_t)(i - base);
+            ++off;
+        }
+        __syncthreads();
+        for (uint32_t q = part; q < total; q += PARTS) {
+            const float2 v = s_p[q];
+            const float key = __fadd_rn(__fmul_rn(c, v.x), __fmul_rn(sn, v.y));
+            const uint32_t i = (uint32_t)(base + s_i[q]);
+            // staged out of index order: equal keys keep the lower index
+            if (!(key <= best) || (key == best && i < bi)) {
+                best = key;
+                bi = i;
+            }
+        }
+        __syncthreads();
+    }
+    s_bk[t] = best;
+    s_bi[t] = bi;
+    __syncthreads();
+    if ((int)t < K) {
+        float k = s_bk[t];
+        uint32_t i = s_bi[t];
+        for (int pp = 1; pp < PARTS; ++pp) take_better(k, i, s_bk[t + pp * K], s_bi[t + pp * K]);
+        if (i != 0xffffffffu) atomicMax(&kc->slot[t], ((unsigned long long)ord_key(k) << 32) | (uint32_t)~i);
+        __threadfence();
+    }
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(&kc->done, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if ((int)t < K) {
+        const unsigned long long packed = atomicExch(&kc->slot[t], 0ull);
+        uint32_t idx = ~(uint32_t)packed;
+        if ((int64_t)idx >= n) idx = 0;   // every direction has a survivor (the octagon's vertices survive)
+        s_ext[t] = idx;
+        if (ext_out) ext_out[t] = idx;
+    }
+    if (t == 0) kc->done = 0;
+    __syncthreads();
+    build_kpoly(p2, K, s_ext, at<KPoly>(ws, L.kpoly));
+}
+
+// The survivors' exact test against the K-gon: bits of kept points strictly
+// inside it are cleared, and the tile's count and its count block's total
+// drop by the number removed (bc: the count pass's grid).
+template <int G>
+__global__ void __launch_bounds__(ST) kx_sv_refine_kernel(const float *__restrict__ pts, int64_t n,
+                                                          const int32_t *kdev, int K, void *ws, Layout L, int32_t bc)
+{
+    __shared__ KPoly sp;
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const int Kr = kdev ? *kdev : K;
+    if (Kr == 8 || !kx_stage_on(oct, kdev, Kr)) return;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(at<KPoly>(ws, L.kpoly));
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+        for (uint32_t w = threadIdx.x; w < sizeof(KPoly) / 4; w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
+    const float2 *p2 = reinterpret_cast<const float2 *>(pts);
+    const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
+    const int64_t per_block = ceil_div(ntiles, (int64_t)bc);
+    const uint32_t t = threadIdx.x, lane = lane_id();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t kb = bits[tile * kFiltThreads + t];
+        uint32_t gone = 0;
+        for (uint32_t b = kb; b; b &= b - 1u) {
+            const int q = __ffs(b) - 1;
+            const float2 v = p2[sv_point<G>(tile * kFiltTile, t, q)];
+            if (!kx_keep(sp, v.x, v.y)) gone |= 1u << q;
+        }
+        if (gone) bits[tile * kFiltThreads + t] = (uint16_t)(kb & ~gone);
+        uint32_t removed = __popc(gone);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) removed += __shfl_xor_sync(0xffffffffu, removed, o);
+        if (lane == 0 && removed) {
+            atomicAdd(&status[tile], 0ull - (unsigned long long)removed);
+            atomicSub(&bsum[tile / per_block], removed);
+        }
+    }
+}
+
+// The learned proposal's choice on the device: K from the arg-max of the
+// MLP's four K-logits (lowest on ties), the offsets (units of pi / K)
+// clipped to +-0.45, the directions at angles 2 pi k / K + offset_k pi / K
+// (cos and sin in binary64, rounded once; a multiple of pi / 4 with zero
+// offset takes the octagon's integer direction).  One warp.
+__global__ void kx_choose_kernel(const float *__restrict__ out, int32_t *kdev, float *dirs)
+{
+    const uint32_t lane = lane_id();
+    int best = 0;
+    for (int i = 1; i < 4; ++i)
+        if (out[i] > out[best]) best = i;   // a NaN logit never wins
+    const int K = 8 << best;
+    for (int k = (int)lane; k < K; k += 32) {
+        float u = out[4 + k];
+        u = fminf(fmaxf(u, -0.45f), 0.45f);
+        if (!(u == u)) u = 0.0f;
+        float cx, cy;
+        if (u == 0.0f && (8 * k) % K == 0) {
+            const int o = 8 * k / K;
+            const int tx[8] = {1, 1, 0, -1, -1, -1, 0, 1}, ty[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+            cx = (float)tx[o];
+            cy = (float)ty[o];
+        } else {
+            const double th = 2.0 * 3.141592653589793 * k / K + (double)u * 3.141592653589793 / K;
+            cx = (float)cos(th);
+            cy = (float)sin(th);
+        }
+        dirs[2 * k] = cx;
+        dirs[2 * k + 1] = cy;
+    }
+    if (lane == 0) *kdev = K;
+}
+
+template <int G>
+cudaError_t launch_kx_sv_stage(const float *pts, int64_t n, const float *dirs, const int32_t *kdev, int K,
+                               uint32_t *ext_out, void *ws, const Layout &L, int64_t bc, cudaStream_t st)
+{
+    const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count() * 4));
+    const unsigned g = (unsigned)grid;
+    probe_before(CH_K_KGON, st);
+    int launched = 0;
+    if (kdev || K == 16) kx_sv_extremes_kernel<16, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
+    if (kdev || K == 32) kx_sv_extremes_kernel<32, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
+    if (kdev || K == 64) kx_sv_extremes_kernel<64, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
+    kx_sv_refine_kernel<G><<<g, ST, 0, st>>>(pts, n, kdev, K, ws, L, (int32_t)bc);
+    note_kernels(CH_K_KGON, launched + 1);
+    probe_after(CH_K_KGON, st);
+    return cudaGetLastError();
+}
+
 template <class Kern>
 int resident(Kern k, int threads)
 {
@@ -428,6 +652,21 @@ cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const 
     else kx_count_kernel<1><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
     note_kernels(CH_K_FILTER, 1);
     probe_after(CH_K_FILTER, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kx_sv(const float *pts, int64_t n, const float *dirs, const int32_t *kdev, int K, uint32_t *ext_out,
+                        void *ws, const Layout &L, int64_t bc, cudaStream_t st)
+{
+    const bool vec = (reinterpret_cast<uintptr_t>(pts) & 15u) == 0;
+    return vec ? launch_kx_sv_stage<2>(pts, n, dirs, kdev, K, ext_out, ws, L, bc, st)
+               : launch_kx_sv_stage<1>(pts, n, dirs, kdev, K, ext_out, ws, L, bc, st);
+}
+
+cudaError_t launch_kx_choose(const float *out, int32_t *kdev, float *dirs, cudaStream_t st)
+{
+    kx_choose_kernel<<<1, 32, 0, st>>>(out, kdev, dirs);
+    note_kernels(CH_K_KGON, 1);
     return cudaGetLastError();
 }
 

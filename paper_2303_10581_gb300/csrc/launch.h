@@ -36,9 +36,18 @@ cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, vo
 // the polygon was built from the data's own extremes (ch_hull,
 // ch_extremes_filter; always so in keys mode), which allows the speculative
 // sweep's candidates; otherwise the vertices are the caller's (ch_filter).
+// A second polygon between the count pass and the fan (two passes only):
+// the K-direction polygon over the octagon's survivors (launch_kx_sv).
+struct KgonStage {
+    const float *dirs;       // device, K directions (cos, sin)
+    const int32_t *kdev;     // device choice of K, or NULL: K below
+    int K;                   // 16, 32 or 64 (8: no stage) when kdev is NULL
+    uint32_t *ext_out;       // device, K vertex indices, or NULL
+};
 cudaError_t launch_filter(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                           float *surv_pts, uint32_t *surv_count, bool keys_mode, cudaStream_t st,
-                          int variant = -1, bool fan = false, bool data_extremes = false);
+                          int variant = -1, bool fan = false, bool data_extremes = false,
+                          const KgonStage *kgon = nullptr);
 
 // the process-wide compaction schedule (ch_filter_variant)
 int filter_variant();
@@ -59,6 +68,14 @@ cudaError_t launch_kx_extremes(const float *pts, int64_t n, const float *dirs, i
                                const Layout &L, cudaStream_t st);
 cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const Layout &L, int64_t *grid,
                             cudaStream_t st);
+
+// a K-direction polygon over the octagon's survivors, refining the count
+// pass's keep bits (bc blocks); K is the host's (16, 32, 64; 8: nothing)
+// or, with kdev, the device's choice.  ext_out (nullable): its vertices.
+cudaError_t launch_kx_sv(const float *pts, int64_t n, const float *dirs, const int32_t *kdev, int K, uint32_t *ext_out,
+                        void *ws, const Layout &L, int64_t bc, cudaStream_t st);
+// the learned proposal's choice from the MLP's 68 outputs: K and directions
+cudaError_t launch_kx_choose(const float *out, int32_t *kdev, float *dirs, cudaStream_t st);
 
 // hull step: the fan test applied to the keep bits, tile counts and block
 // totals that the filter's count pass (filter_blocks blocks) left in ws;

@@ -99,6 +99,23 @@ class Proposal:
         ch_hull_kgon(pts, d, idx, cnt, ws.buf, stream)
         return idx, cnt, K
 
+    def hull_on_device(self, pts, ws, stream=None, sync=True):
+        """ch_hull_learned: features, MLP, the choice of K and directions and
+        the hull with that second polygon, all on the device (no host
+        synchronisation inside the call).  Returns (hull_idx, hull_count,
+        K, directions (64, 2)) -- K and directions read back when sync."""
+        import torch
+        from . import ch_hull_learned
+        n = pts.shape[0]
+        idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
+        dirs = torch.empty(128, dtype=torch.float32, device=pts.device)
+        k = torch.zeros(1, dtype=torch.int32, device=pts.device)
+        ch_hull_learned(pts, self.params, dirs, k, idx, cnt, ws.buf, stream)
+        if not sync:
+            return idx, cnt, k, dirs
+        return idx, cnt, int(k.item()), dirs.cpu().numpy().reshape(64, 2)
+
     # -- training ----------------------------------------------------------
     def train_step(self, X, label, off, mask, lam=1.0, lr=1e-3, scratch=None, loss=None, stream=None):
         import torch

@@ -62,6 +62,7 @@ static void check_single(int64_t n, int64_t sets)
         {"utmp", L.utmp, nn * 4},
         {"spec", L.spec, sizeof(SpecCtrl)},
         {"p0", L.p0, 256},
+        {"learn", L.learn, sizeof(LearnScratch)},
     };
     for (size_t i = 0; i < r.size(); ++i) {
         CHECK(r[i].at % 256 == 0, "n=%lld sets=%lld: %s not 256-aligned", (long long)n, (long long)sets, r[i].name);
