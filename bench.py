@@ -887,14 +887,14 @@ def run_kgon(args):
 
 def learned_record(dev, stream, n, steps, warmup, train_sets, seed):
     """The learned proposal against the plain octagon, end-to-end hull time
-    on the same GPU.  Training labels come from timings of the plain K-gon
-    path (ch_hull_kgon for every K, without offsets and with random ones)
-    on sets of the proposal's families; the MLP trains with the library's
-    kernels; evaluation on one n-point set per family: the proposal
-    (features + MLP + the K-gon hull, the host reading the 68 outputs)
-    against the plain octagon in the same K-gon pipeline (K = 8, no fan) and
-    against ch_hull (octagon filter + the hull step's fan).  All three hulls
-    must be equal."""
+    on the same GPU.  The proposal: the weights trained by
+    ``python -m paper_2303_10581_gb300.learned`` (labels from timings of
+    every choice through the method itself: the octagon with the hull
+    step's fan, or the octagon then a K-gon over its survivors, K = 16, 32,
+    64) when that file exists, else a short training here on 2^20-point
+    sets.  Evaluation on one n-point set per family: ch_hull_learned
+    (features, MLP, choice and hull on the device, no host synchronisation)
+    against ch_hull (octagon + fan).  The hulls must be equal."""
     import numpy as np
     import torch
 
@@ -902,56 +902,57 @@ def learned_record(dev, stream, n, steps, warmup, train_sets, seed):
     import pointgen
     from paper_2303_10581_gb300 import learned
 
-    n_train, per_family = 1 << 20, train_sets
-    prop = learned.Proposal(device=dev, seed=seed)
     t0 = time.perf_counter()
-    ws_small = ch.Workspace(n_train, device=dev)
-    sets = [pointgen.make_family(kind, n_train, seed=10_000 * k + s)
-            for k, kind in enumerate(pointgen.FAMILIES) for s in range(per_family)]
-    X, label, off, mask = learned.make_labels(sets, ws_small, prop, seed=seed)
-    del ws_small, sets
-    hist = prop.train(X, label, off, mask, steps=400, batch=48, lr=3e-3, lam=0.5)
-    train_s = time.perf_counter() - t0
-    counts = np.bincount(label.cpu().numpy(), minlength=4).tolist()
+    if os.path.exists(learned.DEFAULT_WEIGHTS):
+        prop, meta = learned.load_params(learned.DEFAULT_WEIGHTS, device=dev)
+        training = dict(meta, source="weights file " + os.path.relpath(learned.DEFAULT_WEIGHTS, ROOT))
+    else:
+        n_train = 1 << 20
+        prop = learned.Proposal(device=dev, seed=seed)
+        ws_small = ch.Workspace(n_train, device=dev)
+        sets = [pointgen.make_family(kind, n_train, seed=10_000 * k + s)
+                for k, kind in enumerate(pointgen.FAMILIES) for s in range(train_sets)]
+        X, label, off, mask = learned.make_labels(sets, ws_small, prop, seed=seed)
+        del ws_small, sets
+        hist = prop.train(X, label, off, mask, steps=400, batch=48, lr=3e-3, lam=0.5)
+        training = {"source": f"trained here: {len(pointgen.FAMILIES) * train_sets} sets of n=2^20",
+                    "label_counts_K8_16_32_64": np.bincount(label.cpu().numpy(), minlength=4).tolist(),
+                    "final_loss": round(float(np.mean(hist[-20:])), 4)}
+    setup_s = time.perf_counter() - t0
 
     ws = ch.Workspace(n, device=dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-    oct_dirs = torch.from_numpy(learned.directions(8)).to(dev)
 
     def timed(fn):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return round(e0.elapsed_time(e1) / steps, 4), round((time.perf_counter() - t1) * 1e3 / steps, 4)
+        return round(e0.elapsed_time(e1) / steps, 4)
 
     per_family = {}
     for k, kind in enumerate(pointgen.FAMILIES):
         d = torch.from_numpy(pointgen.make_family(kind, n, seed=90 + k)).to(dev)
-        ms_fan, _ = timed(lambda: ch.ch_hull(d, out, cnt, ws.buf, stream))
+        ms_fan = timed(lambda: ch.ch_hull(d, out, cnt, ws.buf, stream))
         h_fan = out[: int(cnt.item())].clone()
-        ms_oct, _ = timed(lambda: ch.ch_hull_kgon(d, oct_dirs, out, cnt, ws.buf, stream))
-        h_oct = out[: int(cnt.item())].clone()
         res = {}
 
         def learned_hull():
-            res["h"] = prop.hull(d, ws, stream)
+            res["h"] = prop.hull_on_device(d, ws, stream, sync=False)
 
-        ms_l, wall_l = timed(learned_hull)
-        idx_l, cnt_l, K = res["h"]
-        h_l = idx_l[: int(cnt_l.item())]
+        ms_l = timed(learned_hull)
+        idx_l, cnt_l, k_l, _ = res["h"]
         ws.check()
-        assert torch.equal(h_fan, h_oct) and torch.equal(h_fan, h_l), kind
-        per_family[kind] = {"learned_ms": ms_l, "learned_wall_ms": wall_l, "learned_K": K,
-                            "octagon_kgon_path_ms": ms_oct, "octagon_with_fan_ms": ms_fan,
-                            "hull_vertices": int(h_fan.numel())}
+        h_l = idx_l[: int(cnt_l.item())]
+        assert torch.equal(h_fan, h_l), kind
+        per_family[kind] = {"learned_ms": ms_l, "learned_K": int(k_l.item()), "octagon_with_fan_ms": ms_fan,
+                            "learned_over_octagon": round(ms_l / ms_fan, 4), "hull_vertices": int(h_fan.numel())}
         del d
     del ws, out
     torch.cuda.synchronize()
@@ -959,10 +960,7 @@ def learned_record(dev, stream, n, steps, warmup, train_sets, seed):
     mean_l = sum(v["learned_ms"] for v in per_family.values()) / len(per_family)
     return {
         "workload": f"one set of n={n} per family: " + ", ".join(pointgen.FAMILIES),
-        "training": f"{len(pointgen.FAMILIES) * train_sets} sets of n=2^20, labels from ch_hull_kgon timings "
-                    f"(K in 8,16,32,64; no / 2 random offsets), 400 Adam steps, batch 48",
-        "label_counts_K8_16_32_64": counts, "final_loss": round(float(np.mean(hist[-20:])), 4),
-        "train_seconds": round(train_s, 1), "learned_ms_mean": round(mean_l, 4),
+        "training": training, "setup_seconds": round(setup_s, 1), "learned_ms_mean": round(mean_l, 4),
         "octagon_with_fan_ms_mean": round(sum(v["octagon_with_fan_ms"] for v in per_family.values())
                                           / len(per_family), 4),
         "per_family": per_family,
@@ -981,8 +979,7 @@ def run_learned(args):
         "value": rec["learned_ms_mean"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "dtype": "f32+exact; MLP bf16 weights, f32 accumulate",
         "data": "synthetic",
-        "config": {k: rec[k] for k in ("workload", "training", "label_counts_K8_16_32_64", "final_loss",
-                                       "train_seconds")},
+        "config": {k: rec[k] for k in ("workload", "training", "setup_seconds")},
         "per_family": rec["per_family"],
     }
     print(json.dumps(line), flush=True)

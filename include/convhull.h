@@ -187,8 +187,9 @@ ch_status ch_hull_octagon_kgon(const float *pts, int64_t n, const float *dirs, i
                                void *stream);
 
 /* The learned proposal end to end without a host synchronisation (not in
- * the paper): the features (ch_kgon_features) and the MLP (ch_mlp_forward)
- * of the set, then on the device K from the arg-max of the four K-logits
+ * the paper): one block computes the features (as ch_kgon_features) and
+ * the MLP (as ch_mlp_forward, each output's sum spread over a warp, so its
+ * rounding may differ in the last bits), then K from the arg-max of the four K-logits
  * and the directions at angles 2 pi k / K + offset_k pi / K (offsets
  * clipped to +-0.45; cos and sin in binary64, rounded once; a multiple of
  * pi / 4 with zero offset takes the octagon's integer direction), then

@@ -183,11 +183,12 @@ namespace {
 // ch_hull's launches with an optional second polygon between the octagon's
 // count pass and the fan
 cudaError_t hull_pipeline(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
-                          const Layout &L, const KgonStage *kg, cudaStream_t st)
+                          const Layout &L, const KgonStage *kg, cudaStream_t st, const void *learn_params = nullptr)
 {
     const int variant = filter_variant();
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
-                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0);
+                                    at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0,
+                                    learn_params);
     if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true, true, kg);
     if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
@@ -241,12 +242,10 @@ extern "C" ch_status ch_hull_learned(const float *pts, int64_t n, const void *pa
         return CH_ERR_ARG;
     const Layout L = make_layout(n);
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
+    // the proposal runs in one more block of the extremes sweep
     LearnScratch *ls = at<LearnScratch>(ws, L.learn);
-    if (ch_status s = ch_kgon_features(pts, n, ls->feat, stream)) return s;
-    if (ch_status s = ch_mlp_forward(ls->feat, 1, params, ls->h1, ls->h2, ls->out, stream)) return s;
-    cudaError_t e = launch_kx_choose(ls->out, &ls->K, ls->dirs, st);
     const KgonStage kg{ls->dirs, &ls->K, 0, nullptr};
-    if (e == cudaSuccess) e = hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st);
+    cudaError_t e = hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st, params);
     if (e == cudaSuccess && dirs_out) e = cudaMemcpyAsync(dirs_out, ls->dirs, sizeof(ls->dirs), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, &ls->K, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     return cuda_status(e);

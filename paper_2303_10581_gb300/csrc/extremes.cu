@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "mlp.cuh"
 
 namespace ch {
 
@@ -297,16 +298,27 @@ __device__ __forceinline__ void spec_warp_point(const SpecBox &b, bool valid, ui
 // filter, whose count and scatter passes test only the candidates
 // (Octagon::spec).  A full segment or a failed check leaves spec = 0 and
 // the filter runs its two passes over all points.
+//
+// learn (ch_hull_learned): one more block than the sweep's runs the learned
+// proposal (mlp.cuh) beside it -- features, MLP and the choice of the second
+// polygon, ready long before the kernels that read it.
 template <bool SPEC>
 __global__ void __launch_bounds__(kExtThreads, 2) extremes_kernel(const float *__restrict__ pts, int64_t n,
                                                                   void *ws, Layout L, uint32_t *ext8_out,
                                                                   int build_polygon, unsigned long long *zero_ptr,
-                                                                  int64_t zero_words, uint32_t cap)
+                                                                  int64_t zero_words, uint32_t cap,
+                                                                  const __nv_bfloat16 *learn)
 {
+    static_assert(kExtThreads == mlp::LT, "the learned block has the sweep's block size");
+    const uint32_t nsweep = gridDim.x - (learn ? 1u : 0u);   // blocks of the sweep
+    if (learn && blockIdx.x == nsweep) {
+        mlp::learned_choice_block(pts, n, learn, at<LearnScratch>(ws, L.learn));
+        return;
+    }
     ExtCtrl *ctrl = at<ExtCtrl>(ws, L.extctrl);
     // clear what the following kernels of this call expect to be zero
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gthreads = (int64_t)nsweep * blockDim.x;
     for (int64_t w = gtid; w < zero_words; w += gthreads) zero_ptr[w] = 0ull;
 
     bool nan_seen = false;
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(kExtThreads, 2) extremes_kernel(const float *_
     // next tile streams into L2 while this one is reduced
     constexpr int U = kExtPairs / kExtThreads;
     const int64_t ntiles = ceil_div(npairs, (int64_t)kExtPairs);
-    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t per = ceil_div(ntiles, (int64_t)nsweep);
     const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
     const int64_t nfull = npairs / kExtPairs;   // the ragged last tile is taken point by point below
     const int64_t t1f = min(t1, nfull);
@@ -456,7 +468,7 @@ __global__ void __launch_bounds__(kExtThreads, 2) extremes_kernel(const float *_
         if constexpr (SPEC)
             if (spec_live) spec_warp_point(box, mine, 0, x, y, wcnt, cap, sc, cidx, cpt, slice0);
     }
-    if (blockIdx.x == gridDim.x - 1 && warp == 0 && (n - head) % 2 == 1) {
+    if (blockIdx.x == nsweep - 1 && warp == 0 && (n - head) % 2 == 1) {
         const bool mine = lane == 0;
         const int64_t i = n - 1;
         const float x = pts[2 * i], y = pts[2 * i + 1];
@@ -532,7 +544,7 @@ __global__ void __launch_bounds__(kExtThreads, 2) extremes_kernel(const float *_
         if (lane == 0 && s_nonfinite) atomicOr(&ctrl->nonfinite, 1u);
         __threadfence();
         __syncwarp();
-        if (lane == 0) s_last = atomicAdd(&ctrl->ext_done, 1u) == gridDim.x - 1;
+        if (lane == 0) s_last = atomicAdd(&ctrl->ext_done, 1u) == nsweep - 1;
     }
     __syncthreads();
     if (!s_last || warp != 0) return;
@@ -923,34 +935,37 @@ int extremes_per_sm()
 
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
-                            cudaStream_t st, bool spec)
+                            cudaStream_t st, bool spec, const void *learn_params)
 {
+    const __nv_bfloat16 *learn = static_cast<const __nv_bfloat16 *>(learn_params);
+    const unsigned extra = learn ? 1u : 0u;
     const int64_t pairs = (n + 1) / 2;
     const int64_t tiles = ceil_div(pairs, (int64_t)kExtPairs);
     // the speculative sweep: large sets only, one candidate segment per
     // block inside the second sort buffers
     if (spec && build_polygon && n >= kSpecMinN) {
-        int64_t blocks = std::min<int64_t>(tiles, (int64_t)sm_count() * extremes_per_sm<true>());
+        // one wave with the learned block: it must not wait for a slot
+        int64_t blocks = std::min<int64_t>(tiles, (int64_t)sm_count() * extremes_per_sm<true>() - extra);
         if (blocks < 1) blocks = 1;
         const int64_t cap = n / kSpecCapDiv / (blocks * kSpecWarps);   // candidate slots per warp slice
         if (blocks <= kSpecMaxSeg && cap >= 16) {
             probe_before(CH_K_EXTREMES, st);
             spec_sample_kernel<<<kSampleBlocks, kSampleThreads, 0, st>>>(pts, n, ws, L, (uint32_t)blocks,
                                                                          (uint32_t)cap);
-            extremes_kernel<true><<<(unsigned)blocks, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, 1, zero_ptr,
-                                                                           zero_words, (uint32_t)cap);
+            extremes_kernel<true><<<(unsigned)blocks + extra, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, 1, zero_ptr,
+                                                                                   zero_words, (uint32_t)cap, learn);
             note_kernels(CH_K_EXTREMES, 2);
             probe_after(CH_K_EXTREMES, st);
             return cudaGetLastError();
         }
     }
-    int64_t blocks = tiles;   // one wave: every block resident
-    const int64_t cap = (int64_t)sm_count() * extremes_per_sm<false>();
+    int64_t blocks = tiles;   // one wave: every block (and the learned one) resident
+    const int64_t cap = (int64_t)sm_count() * extremes_per_sm<false>() - extra;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     probe_before(CH_K_EXTREMES, st);
-    extremes_kernel<false><<<(unsigned)blocks, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, build_polygon ? 1 : 0,
-                                                                     zero_ptr, zero_words, 0u);
+    extremes_kernel<false><<<(unsigned)blocks + extra, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, build_polygon ? 1 : 0,
+                                                                             zero_ptr, zero_words, 0u, learn);
     note_kernels(CH_K_EXTREMES, 1);
     probe_after(CH_K_EXTREMES, st);
     return cudaGetLastError();

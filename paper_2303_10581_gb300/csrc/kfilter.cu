@@ -406,21 +406,30 @@ __device__ __forceinline__ int64_t sv_point(int64_t base, uint32_t t, int q)
 
 // Survivors of each tile are staged in shared memory (compacted), then
 // thread t keeps the best of direction t mod K over its share of them.
+struct SvSmem {
+    float2 p[kFiltTile];
+    uint16_t i[kFiltTile];   // index - base
+    uint32_t w[ST / 32];
+    float bk[ST];
+    uint32_t bi[ST];
+    uint32_t ext[kMaxDirs];
+    int last;
+};
+
 template <int K, int G>
-__global__ void __launch_bounds__(ST) kx_sv_extremes_kernel(const float *__restrict__ pts, int64_t n,
-                                                            const float *__restrict__ dirs, const int32_t *kdev,
-                                                            uint32_t *ext_out, void *ws, Layout L)
+__device__ __forceinline__ void kx_sv_extremes_body(SvSmem &sm, const float *__restrict__ pts, int64_t n,
+                                                    const float *__restrict__ dirs, const int32_t *kdev,
+                                                    uint32_t *ext_out, void *ws, const Layout &L)
 {
     static_assert(K >= 8 && K <= kMaxDirs && ST % K == 0 && ST == kFiltThreads, "directions split the block evenly");
     constexpr int PARTS = ST / K;
-    __shared__ float2 s_p[kFiltTile];
-    __shared__ uint16_t s_i[kFiltTile];   // index - base
-    __shared__ uint32_t s_w[ST / 32];
-    __shared__ uint32_t s_total;
-    __shared__ float s_bk[ST];
-    __shared__ uint32_t s_bi[ST];
-    __shared__ uint32_t s_ext[kMaxDirs];
-    __shared__ int s_last;
+    float2 *s_p = sm.p;
+    uint16_t *s_i = sm.i;
+    uint32_t *s_w = sm.w;
+    float *s_bk = sm.bk;
+    uint32_t *s_bi = sm.bi;
+    uint32_t *s_ext = sm.ext;
+    int &s_last = sm.last;
     Octagon *oct = at<Octagon>(ws, L.oct);
     if (!kx_stage_on(oct, kdev, K)) return;
     KxCtrl *kc = at<KxCtrl>(ws, L.kxctrl);
@@ -504,6 +513,24 @@ __global__ void __launch_bounds__(ST) kx_sv_extremes_kernel(const float *__restr
     build_kpoly(p2, K, s_ext, at<KPoly>(ws, L.kpoly));
 }
 
+// KT: the host's K, or 0: the device's choice (*kdev), dispatched here so
+// one launch serves every K.
+template <int KT, int G>
+__global__ void __launch_bounds__(ST) kx_sv_extremes_kernel(const float *__restrict__ pts, int64_t n,
+                                                            const float *__restrict__ dirs, const int32_t *kdev,
+                                                            uint32_t *ext_out, void *ws, Layout L)
+{
+    __shared__ SvSmem sm;
+    if constexpr (KT == 0) {
+        const int K = *kdev;   // uniform
+        if (K == 16) kx_sv_extremes_body<16, G>(sm, pts, n, dirs, kdev, ext_out, ws, L);
+        else if (K == 32) kx_sv_extremes_body<32, G>(sm, pts, n, dirs, kdev, ext_out, ws, L);
+        else if (K == 64) kx_sv_extremes_body<64, G>(sm, pts, n, dirs, kdev, ext_out, ws, L);
+    } else {
+        kx_sv_extremes_body<KT, G>(sm, pts, n, dirs, kdev, ext_out, ws, L);
+    }
+}
+
 // The survivors' exact test against the K-gon: bits of kept points strictly
 // inside it are cleared, and the tile's count and its count block's total
 // drop by the number removed (bc: the count pass's grid).
@@ -547,53 +574,22 @@ __global__ void __launch_bounds__(ST) kx_sv_refine_kernel(const float *__restric
     }
 }
 
-// The learned proposal's choice on the device: K from the arg-max of the
-// MLP's four K-logits (lowest on ties), the offsets (units of pi / K)
-// clipped to +-0.45, the directions at angles 2 pi k / K + offset_k pi / K
-// (cos and sin in binary64, rounded once; a multiple of pi / 4 with zero
-// offset takes the octagon's integer direction).  One warp.
-__global__ void kx_choose_kernel(const float *__restrict__ out, int32_t *kdev, float *dirs)
-{
-    const uint32_t lane = lane_id();
-    int best = 0;
-    for (int i = 1; i < 4; ++i)
-        if (out[i] > out[best]) best = i;   // a NaN logit never wins
-    const int K = 8 << best;
-    for (int k = (int)lane; k < K; k += 32) {
-        float u = out[4 + k];
-        u = fminf(fmaxf(u, -0.45f), 0.45f);
-        if (!(u == u)) u = 0.0f;
-        float cx, cy;
-        if (u == 0.0f && (8 * k) % K == 0) {
-            const int o = 8 * k / K;
-            const int tx[8] = {1, 1, 0, -1, -1, -1, 0, 1}, ty[8] = {0, 1, 1, 1, 0, -1, -1, -1};
-            cx = (float)tx[o];
-            cy = (float)ty[o];
-        } else {
-            const double th = 2.0 * 3.141592653589793 * k / K + (double)u * 3.141592653589793 / K;
-            cx = (float)cos(th);
-            cy = (float)sin(th);
-        }
-        dirs[2 * k] = cx;
-        dirs[2 * k + 1] = cy;
-    }
-    if (lane == 0) *kdev = K;
-}
-
 template <int G>
 cudaError_t launch_kx_sv_stage(const float *pts, int64_t n, const float *dirs, const int32_t *kdev, int K,
                                uint32_t *ext_out, void *ws, const Layout &L, int64_t bc, cudaStream_t st)
 {
     const int64_t ntiles = ceil_div(n, (int64_t)kFiltTile);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count() * 4));
+    // the device's choice is mostly "no second polygon": a grid of one block
+    // per SM keeps the two launches that then return at once short
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count() * (kdev ? 1 : 4)));
     const unsigned g = (unsigned)grid;
     probe_before(CH_K_KGON, st);
-    int launched = 0;
-    if (kdev || K == 16) kx_sv_extremes_kernel<16, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
-    if (kdev || K == 32) kx_sv_extremes_kernel<32, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
-    if (kdev || K == 64) kx_sv_extremes_kernel<64, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L), ++launched;
+    if (kdev) kx_sv_extremes_kernel<0, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L);
+    else if (K == 16) kx_sv_extremes_kernel<16, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L);
+    else if (K == 32) kx_sv_extremes_kernel<32, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L);
+    else kx_sv_extremes_kernel<64, G><<<g, ST, 0, st>>>(pts, n, dirs, kdev, ext_out, ws, L);
     kx_sv_refine_kernel<G><<<g, ST, 0, st>>>(pts, n, kdev, K, ws, L, (int32_t)bc);
-    note_kernels(CH_K_KGON, launched + 1);
+    note_kernels(CH_K_KGON, 2);
     probe_after(CH_K_KGON, st);
     return cudaGetLastError();
 }
@@ -663,11 +659,6 @@ cudaError_t launch_kx_sv(const float *pts, int64_t n, const float *dirs, const i
                : launch_kx_sv_stage<1>(pts, n, dirs, kdev, K, ext_out, ws, L, bc, st);
 }
 
-cudaError_t launch_kx_choose(const float *out, int32_t *kdev, float *dirs, cudaStream_t st)
-{
-    kx_choose_kernel<<<1, 32, 0, st>>>(out, kdev, dirs);
-    note_kernels(CH_K_KGON, 1);
-    return cudaGetLastError();
-}
+
 
 }  // namespace ch

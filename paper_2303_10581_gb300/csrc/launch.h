@@ -17,13 +17,15 @@ void probe_before(int kid, cudaStream_t st);
 void note_kernels(int kid, int count);
 void probe_after(int kid, cudaStream_t st);
 
+// learn_params (the MLP's BF16 parameters, ch_hull_learned): one more block
+// runs the learned proposal into the workspace's LearnScratch.
 // spec (with build_polygon, on large sets): the speculative single sweep --
 // a sample octagon first, then the sweep writes the points it cannot prove
 // inside it as candidates; when its last block proves the sample octagon
 // inside the final one (Octagon::spec), the filter's passes test only them
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
-                            cudaStream_t st, bool spec = false);
+                            cudaStream_t st, bool spec = false, const void *learn_params = nullptr);
 
 cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, void *ws, const Layout &L,
                            unsigned long long *zero_ptr, int64_t zero_words, cudaStream_t st);
@@ -74,8 +76,10 @@ cudaError_t launch_kx_count(const float *pts, int64_t n, int K, void *ws, const 
 // or, with kdev, the device's choice.  ext_out (nullable): its vertices.
 cudaError_t launch_kx_sv(const float *pts, int64_t n, const float *dirs, const int32_t *kdev, int K, uint32_t *ext_out,
                         void *ws, const Layout &L, int64_t bc, cudaStream_t st);
-// the learned proposal's choice from the MLP's 68 outputs: K and directions
-cudaError_t launch_kx_choose(const float *out, int32_t *kdev, float *dirs, cudaStream_t st);
+// the learned proposal in one block (mlp.cu): features, the MLP, the choice
+// of K and the directions, into the workspace's LearnScratch
+cudaError_t launch_learned_choice(const float *pts, int64_t n, const void *params, void *ws, const Layout &L,
+                                  cudaStream_t st);
 
 // hull step: the fan test applied to the keep bits, tile counts and block
 // totals that the filter's count pass (filter_blocks blocks) left in ws;

@@ -21,25 +21,14 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "mlp.cuh"
 
 namespace ch {
 namespace {
 
-constexpr int kGrid = 32;
-constexpr int kIn = kGrid * kGrid;   // 1024
-constexpr int kHid = 64;
-constexpr int kOut = 4 + 64;         // K-logits, offsets
-constexpr int kSample = 4096;
+using namespace mlp;
 
-constexpr int oW1 = 0;
-constexpr int oB1 = oW1 + kHid * kIn;
-constexpr int oW2 = oB1 + kHid;
-constexpr int oB2 = oW2 + kHid * kHid;
-constexpr int oW3 = oB2 + kHid;
-constexpr int oB3 = oW3 + kOut * kHid;
-constexpr int kParams = oB3 + kOut;
 
-__device__ __forceinline__ float wf(const __nv_bfloat16 *P, int i) { return __bfloat162float(P[i]); }
 
 // One block of 1024 threads per point set.
 __global__ void __launch_bounds__(1024) features_kernel(const float *__restrict__ pts, int64_t n, float *__restrict__ feat)
@@ -237,11 +226,34 @@ __global__ void adam_kernel(float *__restrict__ Wm, const float *__restrict__ G,
 }
 
 }  // namespace
+
+namespace {
+
+// ch_hull_learned's proposal in one block (mlp.cuh)
+__global__ void __launch_bounds__(mlp::LT) learned_choice_kernel(const float *__restrict__ pts, int64_t n,
+                                                                 const __nv_bfloat16 *__restrict__ P, LearnScratch *ls)
+{
+    mlp::learned_choice_block(pts, n, P, ls);
+}
+
+}  // namespace
+
+cudaError_t launch_learned_choice(const float *pts, int64_t n, const void *params, void *ws, const Layout &L,
+                                  cudaStream_t st)
+{
+    probe_before(CH_K_KGON, st);
+    learned_choice_kernel<<<1, mlp::LT, 0, st>>>(pts, n, static_cast<const __nv_bfloat16 *>(params),
+                                                at<LearnScratch>(ws, L.learn));
+    note_kernels(CH_K_KGON, 1);
+    probe_after(CH_K_KGON, st);
+    return cudaGetLastError();
+}
+
 }  // namespace ch
 
 using namespace ch;
 
-extern "C" int32_t ch_mlp_param_count(void) { return kParams; }
+extern "C" int32_t ch_mlp_param_count(void) { return mlp::kParams; }
 
 extern "C" ch_status ch_kgon_features(const float *pts, int64_t n, float *feat, void *stream)
 {

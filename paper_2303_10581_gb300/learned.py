@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 
 import numpy as np
 
@@ -166,11 +167,37 @@ def time_hull_kgon(pts, dirs, ws, reps: int = 2) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def make_labels(point_sets, ws, proposal: Proposal, candidates: int = 2, seed: int = 0):
-    """Training tensors from timings of the plain K-gon path: for every set,
+def time_hull_choice(pts, K, dirs, ws, reps: int = 2) -> float:
+    """ms of one hull with the octagon and (K > 8) the K-gon over its
+    survivors -- ch_hull_octagon_kgon, the pipeline ch_hull_learned runs
+    for that choice (CUDA events, after one warm-up)."""
+    import torch
+    from . import ch_hull_octagon_kgon
+    idx = torch.empty(max(pts.shape[0], 1), dtype=torch.int32, device=pts.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
+
+    def call():
+        ch_hull_octagon_kgon(pts, dirs, K, None, idx, cnt, ws.buf)
+
+    call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def make_labels(point_sets, ws, proposal: Proposal, candidates: int = 2, seed: int = 0, pipeline: str = "octagon"):
+    """Training tensors from timings of the method itself: for every set,
     its features; label = the K whose best candidate polygon (no offsets, or
     one of ``candidates`` random offset vectors) gave the fastest hull; the
-    offset target is that candidate's offsets (in units of pi / K)."""
+    offset target is that candidate's offsets (in units of pi / K).
+    pipeline "octagon": the hull ch_hull_learned runs for each choice
+    (K = 8: the octagon with the hull step's fan, i.e. ch_hull; K > 8: the
+    K-gon over the octagon's survivors as well); "kgon": ch_hull_kgon (the
+    K-gon alone, no fan)."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     X, lab, off = [], [], []
@@ -179,9 +206,11 @@ def make_labels(point_sets, ws, proposal: Proposal, candidates: int = 2, seed: i
         X.append(proposal.features(d).clone())
         best = (math.inf, 0, np.zeros(N_OFF))
         for ki, K in enumerate(KS):
-            cands = [np.zeros(K)] + [rng.uniform(-SPREAD, SPREAD, K) for _ in range(candidates)]
+            n_c = 0 if (pipeline == "octagon" and K == 8) else candidates
+            cands = [np.zeros(K)] + [rng.uniform(-SPREAD, SPREAD, K) for _ in range(n_c)]
             for u in cands:
-                t = time_hull_kgon(d, torch.from_numpy(directions(K, u)).to(d.device), ws)
+                dirs = torch.from_numpy(directions(K, u)).to(d.device)
+                t = (time_hull_choice(d, K, dirs, ws) if pipeline == "octagon" else time_hull_kgon(d, dirs, ws))
                 if t < best[0]:
                     pad = np.zeros(N_OFF)
                     pad[:K] = u
@@ -193,3 +222,86 @@ def make_labels(point_sets, ws, proposal: Proposal, candidates: int = 2, seed: i
     return (torch.stack(X), torch.tensor(lab, dtype=torch.int32, device=dev),
             torch.tensor(np.array(off), dtype=torch.float32, device=dev),
             torch.ones(len(lab), dtype=torch.float32, device=dev))
+
+
+def save_params(proposal: Proposal, path: str, meta: dict) -> None:
+    """The BF16 parameters (as their 16-bit patterns) and a description."""
+    import json
+    import torch
+    bits = proposal.params.view(torch.int16).cpu().numpy().astype(np.uint16)
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    np.savez_compressed(path, params=bits, meta=json.dumps(meta))
+
+
+def load_params(path: str, device="cuda"):
+    """(Proposal with the saved BF16 parameters, their description)."""
+    import json
+    import torch
+    z = np.load(path)
+    prop = Proposal(device=device)
+    bits = torch.from_numpy(z["params"].astype(np.int16)).to(prop.device)
+    assert bits.numel() == prop.n_params, "parameter count"
+    prop.params = bits.view(torch.bfloat16)
+    prop.master = prop.params.to(torch.float32)
+    return prop, json.loads(str(z["meta"]))
+
+
+def train_from_generated(families, sets_per_family: int, n: int, seed: int, steps: int = 800, batch: int = 64,
+                         lr: float = 3e-3, lam: float = 0.5, device="cuda", log=None):
+    """Generates the families' sets (pointgen), labels them by timing every
+    choice through the method itself, trains the MLP; returns (Proposal,
+    description)."""
+    import time
+    import torch
+    import pointgen
+    from . import Workspace
+    t0 = time.perf_counter()
+    prop = Proposal(device=device, seed=seed)
+    ws = Workspace(n, device=device)
+    Xs, labs, offs = [], [], []
+    for k, kind in enumerate(families):
+        for s in range(sets_per_family):
+            p = pointgen.make_family(kind, n, seed=1_000_000 + 10_000 * k + s)
+            X, lab, off, _ = make_labels([p], ws, prop, seed=seed + 7919 * k + s)
+            Xs.append(X)
+            labs.append(lab)
+            offs.append(off)
+            if log and (s + 1) % 100 == 0:
+                log(f"{kind}: {s + 1} sets labelled, {time.perf_counter() - t0:.0f} s")
+    X = torch.cat(Xs)
+    label = torch.cat(labs)
+    off = torch.cat(offs)
+    mask = torch.ones(len(label), dtype=torch.float32, device=prop.device)
+    label_s = time.perf_counter() - t0
+    hist = prop.train(X, label, off, mask, steps=steps, batch=batch, lr=lr, lam=lam, seed=seed)
+    counts = np.bincount(label.cpu().numpy(), minlength=4).tolist()
+    meta = {"families": list(families), "sets_per_family": sets_per_family, "points_per_set": n,
+            "label_counts_K8_16_32_64": counts, "steps": steps, "batch": batch, "lr": lr,
+            "final_loss": round(float(np.mean(hist[-20:])), 4), "label_seconds": round(label_s, 1),
+            "train_seconds": round(time.perf_counter() - t0 - label_s, 1),
+            "labels": "fastest of ch_hull (K=8: octagon + fan) and ch_hull_octagon_kgon with K in 16, 32, 64 "
+                      "(no offsets and 2 random offset vectors each)"}
+    return prop, meta
+
+
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "proposal.npz")
+
+
+def main():
+    import argparse
+    import pointgen
+    ap = argparse.ArgumentParser(description="train the learned proposal on generated sets and save its weights")
+    ap.add_argument("--sets-per-family", type=int, default=400)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    a = ap.parse_args()
+    prop, meta = train_from_generated(pointgen.FAMILIES, a.sets_per_family, a.n, a.seed, steps=a.steps,
+                                      log=lambda m: print(m, flush=True))
+    save_params(prop, a.out, meta)
+    print(meta, flush=True)
+
+
+if __name__ == "__main__":
+    main()
