@@ -97,6 +97,10 @@ struct KgonCtrl {                          // zeroed with the control block
 struct Kgon {
     float cx, cy;                          // fan centre, strictly inside the hull
     uint32_t ok;                           // 0: no fan this call
+    uint32_t disk_bad;                     // 1: no disk around the centre is proven inside the fan
+    unsigned long long rho2;               // bits of a lower bound on the squared distance from
+                                           // the centre to the fan's boundary (binary64 >= 0)
+    uint32_t disk_edges;                   // consecutive vertex pairs with v != w
     uint32_t pad;
     float2 v[kFanBins];                    // vertex of every bin (input points)
 };

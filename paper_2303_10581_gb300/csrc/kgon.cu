@@ -49,7 +49,7 @@ constexpr int FITEMS = 8;                // points per thread per tile there
 constexpr int FTILE = FT * FITEMS;       // 4096
 constexpr int CT = 1024;                 // threads per block of the refine pass: four
 constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, each with its own tiles
-constexpr int64_t kBinTiles = 6144;      // the bins see about this many evenly spaced tiles (25 M points)
+constexpr int64_t kBinTiles = 1536;      // the bins see every min(4, tiles / kBinTiles)-th tile (at least every tile)
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
 static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     __syncthreads();
     const float cx = oct->cx, cy = oct->cy;
     const int64_t ntiles = ceil_div(n, FTILE);
-    const int64_t stride = std::max<int64_t>(1, ntiles / kBinTiles);   // every stride-th tile
+    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(4, ntiles / kBinTiles));   // every stride-th tile
     const int64_t nsamp = ceil_div(ntiles, stride);
     for (int64_t k = blockIdx.x; k < nsamp; k += gridDim.x) {
         const int64_t base = k * stride * FTILE;
@@ -260,7 +260,43 @@ __global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__
         g->cx = cx;
         g->cy = cy;
         g->ok = 1u;
+        g->disk_bad = 0u;
+        g->disk_edges = 0u;
+        g->rho2 = 0x7ff0000000000000ull;   // +inf until the estimate kernel bounds it
     }
+}
+
+// A disk around the centre inside the fan: the fan's triangles (c, v, w) of
+// consecutive vertices turn counter-clockwise around c (bins in angular
+// order), so when every triangle with v != w is proven strictly
+// counter-clockwise their union is a polygon winding once around c, and
+// the open disk of radius rho < the distance from c to each of its edges
+// (segments [v, w], or the point v when v == w) lies in its interior,
+// hence strictly inside the hull.  The distance to a segment is the
+// distance to its nearer end when the foot of the perpendicular from c
+// provably falls outside it, else at least the distance to its line.
+// Binary64 with slack: cross and dot products lose at most 2^-50 of the
+// sum of their terms' magnitudes, squares and the quotient 2^-40.  Returns
+// the lower bound on the squared distance to edge (v, w), or -1 when the
+// triangle is not proven counter-clockwise.
+__device__ __forceinline__ double disk_bound(float cx, float cy, float2 v, float2 w)
+{
+    const double ux = (double)cx - v.x, uy = (double)cy - v.y;   // c - v
+    const double dv = (ux * ux + uy * uy) * (1.0 - 0x1p-40);
+    if (v.x == w.x && v.y == w.y) return dv;
+    const double ex = (double)w.x - v.x, ey = (double)w.y - v.y;   // w - v
+    const double t1 = ex * uy, t2 = ey * ux;
+    const double lo = (t1 - t2) - (fabs(t1) + fabs(t2)) * 0x1p-50;   // c strictly left of v -> w
+    if (!(lo > 0.0)) return -1.0;
+    const double len2 = ex * ex + ey * ey;
+    const double d1 = ex * ux, d2 = ey * uy;
+    const double dot = d1 + d2, derr = (fabs(d1) + fabs(d2)) * 0x1p-50;   // (c - v) . (w - v)
+    if (dot < -derr) return dv;   // the foot lies before v: v is the nearest point
+    if (dot > len2 * (1.0 + 0x1p-40) + derr) {   // after w
+        const double zx = (double)cx - w.x, zy = (double)cy - w.y;
+        return (zx * zx + zy * zy) * (1.0 - 0x1p-40);
+    }
+    return lo * lo / (len2 * (1.0 + 0x1p-40)) * (1.0 - 0x1p-40);
 }
 
 // About 2^16 evenly spaced input points.  With f the share of them inside
@@ -302,6 +338,29 @@ __global__ void __launch_bounds__(256) fan_estimate_kernel(const float *__restri
         atomicAdd(&kc->inside, a);
         atomicAdd(&kc->sample, b);
     }
+    // the disk around the centre (disk_bound), min over all bins
+    Kgon *gw = at<Kgon>(ws, L.kgon);
+    double mn = __longlong_as_double(0x7ff0000000000000ll);
+    bool bad = false;
+    uint32_t edges = 0;
+    for (int b = (int)(blockIdx.x * 256 + threadIdx.x); b < kFanBins; b += (int)(gridDim.x * 256)) {
+        const float2 v = g->v[b], w = g->v[next_bin(b)];
+        const double d = disk_bound(g->cx, g->cy, v, w);
+        if (d < 0.0) bad = true;
+        else mn = fmin(mn, d);
+        edges += (v.x != w.x || v.y != w.y) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        edges += __shfl_xor_sync(0xffffffffu, edges, o);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane_id() == 0) {
+        atomicMin(&gw->rho2, (unsigned long long)__double_as_longlong(mn));   // >= 0: bits order as values
+        if (bad) atomicOr(&gw->disk_bad, 1u);
+        if (edges) atomicAdd(&gw->disk_edges, edges);
+    }
 }
 
 __device__ __forceinline__ bool fan_worth(const KgonCtrl *kc, int64_t n, uint32_t s)
@@ -321,10 +380,12 @@ __device__ __forceinline__ int64_t item_point(int64_t base, uint32_t t, int q)
 // Fan test of one half (items 8 half .. 8 half + 7) of a filter thread's
 // kept points.  Returns the bits (at item positions) of kept points strictly
 // inside the fan.  The coordinates of the few undecided points are read
-// again for the exact test, so none stay live across it.
+// again for the exact test, so none stay live across it.  Called by every
+// lane of the warp (a warp-wide reduction picks the path).
 template <int G>
 __device__ __forceinline__ uint32_t refine_half(const float *__restrict__ pts, int64_t n, int64_t base, uint32_t t,
-                                                uint32_t kb, int half, const float2 *sv, float cx, float cy)
+                                                uint32_t kb, int half, const float2 *sv, float cx, float cy,
+                                                float rho2t, bool &use_disk)
 {
     float px[8], py[8];
 #pragma unroll
@@ -360,15 +421,45 @@ __device__ __forceinline__ uint32_t refine_half(const float *__restrict__ pts, i
         }
     }
     const uint32_t live = (kb >> (8 * half)) & 0xffu;
-    uint32_t in = 0, und = 0;
+    // the disk around the centre first: r2 < rho2t proves |p - c|^2 < rho^2
+    // (rho2t is rho^2 less 2^-20 of it, rounded down, which covers the
+    // rounding of r2); when few of a lane's points lie outside the disk the
+    // fan test visits only those
+    // (use_disk, warp-uniform: a warp whose first half-tile finds fewer than
+    // a quarter of its kept points in the disk stops testing it)
+    uint32_t outd = live;
+    if (use_disk) {
+        outd = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float dx = __fsub_rn(px[k], cx), dy = __fsub_rn(py[k], cy);
+            const float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+            outd |= (r2 < rho2t ? 0u : 1u) << k;
+        }
+        outd &= live;
+        const unsigned hits = __reduce_add_sync(0xffffffffu, (unsigned)__popc(live & ~outd));
+        const unsigned tried = __reduce_add_sync(0xffffffffu, (unsigned)__popc(live));
+        if (4u * hits < tried) use_disk = false;
+    }
+    uint32_t in = live & ~outd;
+    if (__reduce_max_sync(0xffffffffu, (unsigned)__popc(outd)) <= 2u) {
+        for (uint32_t b = outd; b; b &= b - 1u) {
+            const int k = __ffs(b) - 1;
+            const float2 p = reinterpret_cast<const float2 *>(pts)[item_point<G>(base, t, 8 * half + k)];
+            if (fan_inside(sv, cx, cy, p)) in |= 1u << k;
+        }
+        return in << (8 * half);
+    }
+    uint32_t und = 0;
+    in = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int f = fan_signs_f32(sv, cx, cy, px[k], py[k]);
         in |= (f == 1 ? 1u : 0u) << k;
         und |= (f == 2 ? 1u : 0u) << k;
     }
-    in &= live;
-    und &= live;
+    in = (in & live) | (live & ~outd);
+    und &= outd;
     while (und) {
         const int k = __ffs(und) - 1;
         und &= und - 1u;
@@ -402,6 +493,12 @@ __global__ void __launch_bounds__(CT, 1) fan_refine_kernel(const float *__restri
         for (int i = threadIdx.x; i < kFanBins / 2; i += CT) dst[i] = __ldg(src + i);
     }
     const float cx = g->cx, cy = g->cy;
+    // -1: no disk (the test never passes for r2 >= 0)
+    // (the triangles wind around c only with three distinct vertices or more)
+    const float rho2t = (g->disk_bad || g->disk_edges < 3u)
+                            ? -1.0f
+                            : __double2float_rd(__longlong_as_double((long long)g->rho2) * (1.0 - 0x1p-20));
+    bool use_disk = rho2t > 0.0f;
     __syncthreads();
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
@@ -421,9 +518,11 @@ __global__ void __launch_bounds__(CT, 1) fan_refine_kernel(const float *__restri
         }
         const uint32_t kb = bits[tile * kFiltThreads + t];
         uint32_t in = 0;
+        // every lane takes both halves (refine_half has a warp-wide
+        // reduction; a half without kept points costs little)
 #pragma unroll 1
         for (int half = 0; half < 2; ++half)
-            if ((kb >> (8 * half)) & 0xffu) in |= refine_half<G>(pts, n, base, t, kb, half, sv, cx, cy);
+            in |= refine_half<G>(pts, n, base, t, kb, half, sv, cx, cy, rho2t, use_disk);
         if (in) bits[tile * kFiltThreads + t] = (uint16_t)(kb & ~in);
         uint32_t removed = __popc(in);
 #pragma unroll
