@@ -545,6 +545,19 @@ __device__ __forceinline__ int orient_f32(float ax, float ay, float bx, float by
     return detsum <= 3.0e38f ? o : 2;
 }
 
+// orient_f32 of (a, b, c) given the rounded differences a - c = (acx, acy)
+// and b - c = (bcx, bcy): the same arithmetic after the subtractions.
+__device__ __forceinline__ int orient_f32_ref(float acx, float acy, float bcx, float bcy)
+{
+    float detleft = __fmul_rn(acx, bcy);
+    float detright = __fmul_rn(acy, bcx);
+    float det = __fsub_rn(detleft, detright);
+    float detsum = __fadd_rn(fabsf(detleft), fabsf(detright));
+    float eb = __fmaf_ru(detsum, 2.384185791015625e-07f /* 2^-22 */, 7.174648137343064e-43f /* 2^-140 */);
+    const int o = det > eb ? 1 : (-det > eb ? -1 : 2);
+    return detsum <= 3.0e38f ? o : 2;
+}
+
 // The tiers after binary32: exact differences, binary64, expansions.
 __device__ __forceinline__ int orient_rest(float ax, float ay, float bx, float by, float cx, float cy)
 {
@@ -567,6 +580,12 @@ __device__ __forceinline__ int orient(float ax, float ay, float bx, float by, fl
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// The line holding `p` into L2 (one lane's hint; nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ---------------------------------------------------------------------------

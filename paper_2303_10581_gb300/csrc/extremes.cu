@@ -605,6 +605,7 @@ constexpr int kSampleBlocks = 32;
 constexpr int kSampleThreads = 256;
 constexpr int kSampleRun = kSampleThreads * 8;
 constexpr double kP0Shrink = 0.9;
+constexpr int kSpecProbe = 1024;   // points tested against A before the sweep
 
 __device__ void build_spec_box(const float (&kmax)[8], SpecBox *out)
 {
@@ -707,15 +708,37 @@ __global__ void __launch_bounds__(kSampleThreads) spec_sample_kernel(const float
     __syncwarp();
     if (lane == 0) s_last = atomicAdd(&sc->sample_done, 1u) == gridDim.x - 1;
     __syncwarp();
-    if (!s_last || lane != 0) return;
+    if (!s_last) return;
     __threadfence();
-    float kmax[8];
-    for (int j = 0; j < 8; ++j) kmax[j] = key_float(atomicExch(&sc->kmax[j], 0u));
-    sc->sample_done = 0u;
-    sc->fail = 0u;
-    sc->nseg = nseg;
-    sc->cap = cap;
-    build_spec_box(kmax, at<SpecBox>(ws, L.p0));
+    __shared__ SpecBox s_box;
+    if (lane == 0) {
+        float kmax[8];
+        for (int j = 0; j < 8; ++j) kmax[j] = key_float(atomicExch(&sc->kmax[j], 0u));
+        sc->sample_done = 0u;
+        sc->fail = 0u;
+        sc->nseg = nseg;
+        sc->cap = cap;
+        build_spec_box(kmax, &s_box);
+    }
+    __syncwarp();
+    // the share of kSpecProbe evenly spaced points outside A predicts the
+    // candidates' share: above half the segments' capacity (1 / kSpecCapDiv
+    // of the points) the sweep would most likely overflow them, so it does
+    // not speculate (either way the outcome is checked, not assumed)
+    uint32_t out = 0;
+    if (s_box.ok) {
+        const int64_t stride = n / kSpecProbe;
+        for (int k = (int)lane; k < kSpecProbe; k += 32) {
+            const float2 v = __ldg(p2 + (int64_t)k * stride);
+            out += spec_inside(s_box, v.x, v.y, __fadd_rn(v.x, v.y), __fsub_rn(v.x, v.y)) ? 0u : 1u;
+        }
+    }
+    out = __reduce_add_sync(0xffffffffu, out);
+    if (lane == 0) {
+        SpecBox b = s_box;
+        if (2u * kSpecCapDiv * out > (uint32_t)kSpecProbe) b.ok = 0u;
+        *at<SpecBox>(ws, L.p0) = b;
+    }
 }
 
 // Polygon construction for a caller-supplied ext8 (ch_filter); also clears

@@ -88,28 +88,48 @@ __device__ __forceinline__ bool keep_point(const Octagon &o, float x, float y)
 
 constexpr int NW = kFiltThreads / 32;
 
+// The polygon in shared memory, with the first look's per-edge data packed
+// (one 16-byte and one 4-byte load per point): (ax, ay, dx, dy) and the
+// bound of edge k; an edge of zero length gets zeros and +inf, which never
+// proves a point outside it.
+struct OctSmem : Octagon {
+    float4 e4[8];
+    float eb[8];
+};
+
+// Fills the packed edges of `so` from the polygon `o` (threads 0..7; the
+// caller synchronises before they are read).
+__device__ __forceinline__ void pack_edges(OctSmem &so, const Octagon &o)
+{
+    const uint32_t k = threadIdx.x;
+    if (k < 8) {
+        const bool v = (o.valid >> k) & 1u;
+        so.e4[k] = v ? make_float4(o.ax[k], o.ay[k], o.dx[k], o.dy[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        so.eb[k] = v ? o.bound[k] : __int_as_float(0x7f800000);
+    }
+}
+
 // A point's first look: 0 discard (inside the quick-discard rectangle), 1
 // keep (outside the vertices' box, or proven not strictly left of the edge
-// facing it), 2 deferred (likely strictly inside: every edge must be tested).
+// facing it), 2 deferred (likely strictly inside: every edge must be
+// tested).  The facing edge is the one of p's octant around the box centre,
+// picked without branches; any edge would give the same final decisions
+// (a 1 is a proof, a 2 is tested in full).
 template <bool BOX>
-__device__ __forceinline__ uint32_t first_look(const Octagon &o, float x, float y)
+__device__ __forceinline__ uint32_t first_look(const OctSmem &o, float x, float y)
 {
-    if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) return 0u;
-    if (!o.has_edges || outside_box<BOX>(o, x, y)) return 1u;
     const float ux = x - o.cx, uy = y - o.cy;
-    int e;
-    if (uy >= 0.0f) {
-        if (ux >= 0.0f) e = ux >= uy ? 0 : 1;
-        else e = uy >= -ux ? 2 : 3;
-    } else {
-        if (ux < 0.0f) e = -ux >= -uy ? 4 : 5;
-        else e = -uy >= ux ? 6 : 7;
-    }
-    if (!((o.valid >> e) & 1u)) return 2u;
-    const float u = __fsub_rn(x, o.ax[e]);
-    const float v = __fsub_rn(y, o.ay[e]);
-    const float t = __fsub_rn(__fmul_rn(o.dx[e], v), __fmul_rn(o.dy[e], u));
-    return t < -o.bound[e] ? 1u : 2u;
+    const float aux = fabsf(ux), auy = fabsf(uy);
+    const uint32_t q = uy < 0.0f ? (ux < 0.0f ? 2u : 3u) : (ux < 0.0f ? 1u : 0u);   // quadrant
+    const uint32_t e = 2u * q + ((q & 1u) ? (auy >= aux ? 0u : 1u) : (aux >= auy ? 0u : 1u));
+    const float4 d = o.e4[e];
+    const float u = __fsub_rn(x, d.x);
+    const float v = __fsub_rn(y, d.y);
+    const float t = __fsub_rn(__fmul_rn(d.z, v), __fmul_rn(d.w, u));
+    uint32_t c = t < -o.eb[e] ? 1u : 2u;
+    if (!o.has_edges || outside_box<BOX>(o, x, y)) c = 1u;
+    if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) c = 0u;
+    return c;
 }
 
 // Deferred points, spread over the lanes, would hold whole warps in the
@@ -118,37 +138,37 @@ __device__ __forceinline__ uint32_t first_look(const Octagon &o, float x, float 
 constexpr uint32_t kDeferCap = 32 * kFiltItems;   // every item of the warp
 
 struct FiltQueue {
-    uint32_t cnt;
     uint16_t tag[kDeferCap];   // lane << 4 | item
     uint32_t res[32];          // kept item bits, per lane
 };
 
 __device__ __forceinline__ void queue_reset(FiltQueue &q)
 {
-    const uint32_t lane = lane_id();
-    q.res[lane] = 0u;
-    if (lane == 0) q.cnt = 0u;
+    q.res[lane_id()] = 0u;
     __syncwarp();
 }
 
-// Records item `item` of this lane as deferred (the queue holds every item
-// of the warp, so it cannot overflow).
-__device__ __forceinline__ void defer(FiltQueue &q, uint32_t item)
-{
-    const uint32_t slot = atomicAdd(&q.cnt, 1u);
-    q.tag[slot] = (uint16_t)((lane_id() << 4) | item);
-}
-
-// Tests the queued points (all lanes); returns this lane's keep bits among
-// them and leaves the queue empty.  load(lane, item) reads a point of this
-// warp.
+// Tests this warp's deferred points (dm: this lane's deferred items, all
+// lanes call): they are queued in lane order (an exclusive scan of the
+// lanes' counts; the queue holds every item of the warp), tested 32 at a
+// time, and this lane's keep bits among them are returned.  load(lane,
+// item) reads a point of this warp.
 template <bool BOX, class LoadPoint>
-__device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon &so, bool deferred, LoadPoint load)
+__device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon &so, uint32_t dm, LoadPoint load)
 {
-    if (!__any_sync(0xffffffffu, deferred)) return 0u;   // the common case: nothing queued
+    const uint32_t c = __popc(dm);
+    if (!__any_sync(0xffffffffu, c != 0u)) return 0u;   // the common case: nothing deferred
+    const uint32_t lane = lane_id();
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t slot = incl - c;
+    for (uint32_t m = dm; m; m &= m - 1u) q.tag[slot++] = (uint16_t)((lane << 4) | (uint32_t)(__ffs(m) - 1));
     __syncwarp();
-    const uint32_t total = q.cnt, lane = lane_id();
-    if (total == 0u) return 0u;
     for (uint32_t i = lane; i < total; i += 32) {
         const uint32_t tg = q.tag[i];
         const float2 v = load(tg >> 4, tg & 15u);
@@ -156,18 +176,20 @@ __device__ __forceinline__ uint32_t resolve_deferred(FiltQueue &q, const Octagon
     }
     __syncwarp();
     const uint32_t r = q.res[lane];
+    q.res[lane] = 0u;   // only this lane touches its entry until the next call's barrier
     __syncwarp();
-    queue_reset(q);
     return r;
 }
 
 // Copies the polygon to shared memory; false when the call was aborted
 // (non-finite input or a bad vertex index).
-__device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout &L)
+__device__ __forceinline__ bool load_octagon(OctSmem &so, void *ws, const Layout &L)
 {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(at<Octagon>(ws, L.oct));
-    uint32_t *dst = reinterpret_cast<uint32_t *>(&so);
+    const Octagon *g = at<Octagon>(ws, L.oct);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(g);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(static_cast<Octagon *>(&so));
     for (uint32_t w = threadIdx.x; w < sizeof(Octagon) / 4; w += blockDim.x) dst[w] = src[w];
+    pack_edges(so, *g);
     __syncthreads();
     return !so.abort;
 }
@@ -178,7 +200,7 @@ __device__ __forceinline__ bool load_octagon(Octagon &so, void *ws, const Layout
 // (bit r * G + h); positions past n are not kept.
 template <int G, bool BOX>
 __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int64_t n, int64_t base,
-                                              const Octagon &so, float (&px)[kFiltItems], float (&py)[kFiltItems],
+                                              const OctSmem &so, float (&px)[kFiltItems], float (&py)[kFiltItems],
                                               FiltQueue &fq)
 {
     constexpr int ROWS = kFiltItems / G;
@@ -208,16 +230,15 @@ __device__ __forceinline__ uint32_t load_test(const float *__restrict__ pts, int
                 py[r] = v[r].y;
             }
         }
-        bool deferred = false;
+        uint32_t dm = 0;   // deferred items
 #pragma unroll
         for (int q = 0; q < kFiltItems; ++q) {
             const uint32_t c = first_look<BOX>(so, px[q], py[q]);
-            if (c == 2u) deferred = true;
-            if (c == 1u) keep |= 1u << q;
-            else if (c == 2u) defer(fq, (uint32_t)q);
+            keep |= (c == 1u ? 1u : 0u) << q;
+            dm |= (c == 2u ? 1u : 0u) << q;
         }
         const uint32_t wbase = tid & ~31u;
-        keep |= resolve_deferred<BOX>(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+        keep |= resolve_deferred<BOX>(fq, so, dm, [&](uint32_t ln, uint32_t item) {
             const int64_t i = base + (int64_t)((item / G) * kFiltThreads + wbase + ln) * G + item % G;
             return reinterpret_cast<const float2 *>(pts)[i];
         });
@@ -320,6 +341,117 @@ __device__ __forceinline__ void scatter_tile(uint32_t keep, int64_t base, uint64
     }
 }
 
+// One warp writes the kept points of one tile in point order, from the
+// stored keep bits: the tile's 256 filter threads in eight groups of 32
+// (group k holds threads 32 k + lane), each thread with kFiltItems / G rows
+// of G points (point base + (r * 256 + t) * G + h).  The warp first counts
+// every row's kept points (each row's first output position), asks L2 for
+// all of its lanes' kept points at once, then per group loads the group's
+// kept rows together and writes them (the warps of a block take different
+// tiles and never wait on one another).
+template <int G, bool KEYS>
+__device__ __forceinline__ void scatter_tile_warp(const float *__restrict__ pts, int64_t n,
+                                                  const uint16_t *__restrict__ tbits, int64_t base, uint32_t out_off,
+                                                  uint32_t *surv_idx, float2 *surv_pts, uint32_t *out_keys,
+                                                  unsigned long long *out_pay)
+{
+    constexpr int ROWS = kFiltItems / G;
+    constexpr uint32_t RM = (1u << G) - 1u;   // a row's bits among a thread's 16
+    const uint32_t lane = lane_id(), lt = (1u << lane) - 1u;
+    uint32_t kb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) kb[k] = tbits[k * 32 + lane];
+    uint32_t racc[ROWS];   // next output position of row r
+    {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = kb[2 * j] | (kb[2 * j + 1] << 16);
+        uint32_t run = out_off;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const uint32_t m = (RM << (r * G)) * 0x10001u;
+            uint32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c += __popc(w[j] & m);
+            racc[r] = run;
+            run += __reduce_add_sync(0xffffffffu, c);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            if ((kb[k] >> (r * G)) & RM)
+                prefetch_l2(pts + 2 * (base + (int64_t)(r * kFiltThreads + k * 32 + lane) * G));
+        }
+    }
+    const auto put = [&](uint32_t pos, float x, float y, uint32_t idx) {
+        if constexpr (KEYS) {
+            out_keys[pos] = ord_key(x);
+            out_pay[pos] = ((unsigned long long)ord_key(y) << 32) | idx;
+        } else {
+            surv_idx[pos] = idx;
+            if (surv_pts) surv_pts[pos] = make_float2(x, y);
+        }
+    };
+    // (one group at a time: its bits again from L1, so that the compiler
+    // keeps one group's loads in registers, not all eight)
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t kbk = tbits[k * 32 + lane];
+        if (!__any_sync(0xffffffffu, kbk != 0u)) continue;
+        const uint32_t t = k * 32 + lane;
+        if constexpr (G == 2) {
+            float4 v[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                v[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if ((kbk >> (2 * r)) & 3u) {
+                    const int64_t i = base + (int64_t)(r * kFiltThreads + t) * 2;
+                    if (i + 1 < n) {
+                        v[r] = __ldcs(reinterpret_cast<const float4 *>(pts) + i / 2);
+                    } else {
+                        const float2 a = reinterpret_cast<const float2 *>(pts)[i];
+                        v[r] = make_float4(a.x, a.y, 0.0f, 0.0f);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const uint32_t m = (kbk >> (2 * r)) & 3u;
+                const uint32_t b0 = __ballot_sync(0xffffffffu, m & 1u), b1 = __ballot_sync(0xffffffffu, m & 2u);
+                if (!(b0 | b1)) continue;
+                uint32_t pos = racc[r] + __popc(b0 & lt) + __popc(b1 & lt);
+                racc[r] += __popc(b0) + __popc(b1);
+                const uint32_t idx = (uint32_t)(base + (int64_t)(r * kFiltThreads + t) * 2);
+                if (m & 1u) put(pos++, v[r].x, v[r].y, idx);
+                if (m & 2u) put(pos, v[r].z, v[r].w, idx + 1u);
+            }
+        } else {   // 16 rows of one point: two halves of 8 loads
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float2 v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = 8 * h + q;
+                    v[q] = make_float2(0.0f, 0.0f);
+                    if ((kbk >> r) & 1u) v[q] = __ldcs(reinterpret_cast<const float2 *>(pts) + base + r * kFiltThreads + t);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = 8 * h + q;
+                    const uint32_t m = (kbk >> r) & 1u;
+                    const uint32_t b0 = __ballot_sync(0xffffffffu, m);
+                    if (!b0) continue;
+                    const uint32_t pos = racc[r] + __popc(b0 & lt);
+                    racc[r] += __popc(b0);
+                    if (m) put(pos, v[q].x, v[q].y, (uint32_t)(base + r * kFiltThreads + t));
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void write_count(bool keys, Ctrl *ctrl, uint32_t *surv_count, uint32_t v)
 {
     if (keys) ctrl->surv_count = v;
@@ -335,7 +467,7 @@ __global__ void __launch_bounds__(kFiltThreads) filter_kernel(const float *__res
                                                               float2 *__restrict__ surv_pts,
                                                               uint32_t *__restrict__ surv_count)
 {
-    __shared__ Octagon so;
+    __shared__ OctSmem so;
     __shared__ FiltQueue s_fq[NW];
     queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_off[kFiltItems / G][NW];
@@ -520,15 +652,38 @@ __device__ void spec_scatter(SpecScatterSmem &sm, void *ws, const Layout &L, uin
 // filt_status[t] receives the survivor count of tile t (low 32 bits); the
 // scan turns it into (offset << 32 | count).  Each thread's 16 keep bits go
 // to keep_bits, so the scatter pass does not test again.
+// Per-tile survivor counts of a window of kCountRing tiles, added up in
+// shared memory by the warps as they finish each tile (no barrier per
+// tile: the warps of a block drift apart and their loads overlap), written
+// to filt_status when the window is done.
+constexpr int kCountRing = 256;
+
+// Block-wide sum to thread 0 (s_w: one slot per warp).
+__device__ __forceinline__ uint32_t block_sum_to0(uint32_t v, uint32_t (&s_w)[NW])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane_id() == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += s_w[w];
+    }
+    return t;
+}
+
 template <int G, bool BOX>
-__global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float *__restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(kFiltThreads, 5) filter_count_kernel(const float *__restrict__ pts, int64_t n,
                                                                     void *ws, Layout L)
 {
-    __shared__ Octagon so;
+    __shared__ OctSmem so;
     __shared__ FiltQueue s_fq[NW];
+    __shared__ uint32_t s_cnt[kCountRing];
     queue_reset(s_fq[threadIdx.x >> 5]);
     __shared__ uint32_t s_w[NW];
-    if (!load_octagon(so, ws, L)) return;
+    for (int i = threadIdx.x; i < kCountRing; i += kFiltThreads) s_cnt[i] = 0u;
+    if (!load_octagon(so, ws, L)) return;   // (its barrier also covers s_cnt)
     if constexpr (!BOX) {
         if (so.spec) {   // the speculative sweep proved all but its candidates inside
             spec_count(so, ws, L, s_w);
@@ -538,36 +693,40 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t lane = lane_id();
     // a contiguous range of tiles per block, so the scatter pass finds
     // every tile's output offset from the block totals and its own range
     const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
     const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
-    uint32_t block_total = 0;
-    for (int64_t tile = (int64_t)blockIdx.x * per; tile < t1; ++tile) {
-        if (threadIdx.x == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
-            const int64_t nb = (tile + 1) * kFiltTile;
-            const uint32_t nn = (uint32_t)std::min<int64_t>(kFiltTile, n - nb);
-            if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
+    uint32_t part = 0;   // this thread's share of the block total
+    for (int64_t w0 = (int64_t)blockIdx.x * per; w0 < t1; w0 += kCountRing) {
+        const int64_t w1 = min(t1, w0 + kCountRing);
+        for (int64_t tile = w0; tile < w1; ++tile) {
+            if (threadIdx.x == 0 && tile + 1 < t1) {   // the next tile streams into L2 meanwhile
+                const int64_t nb = (tile + 1) * kFiltTile;
+                const uint32_t nn = (uint32_t)std::min<int64_t>(kFiltTile, n - nb);
+                if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0)
+                    bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
+            }
+            float px[kFiltItems], py[kFiltItems];
+            const uint32_t keep = load_test<G, BOX>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
+            bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
+            uint32_t c = __popc(keep);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0 && c) atomicAdd(&s_cnt[tile - w0], c);
         }
-        float px[kFiltItems], py[kFiltItems];
-        const uint32_t keep = load_test<G, BOX>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
-        bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
-        uint32_t c = __popc(keep);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) s_w[warp] = c;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t t = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) t += s_w[w];
-            status[tile] = t;
-            block_total += t;
+        for (int64_t i = threadIdx.x; i < w1 - w0; i += kFiltThreads) {
+            const uint32_t v = s_cnt[i];
+            status[w0 + i] = v;
+            s_cnt[i] = 0u;
+            part += v;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = block_total;
+    const uint32_t total = block_sum_to0(part, s_w);
+    if (threadIdx.x == 0) at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = total;
 }
 
 // Second pass, launched with the count pass's grid: block b owns the same
@@ -575,13 +734,12 @@ __global__ void __launch_bounds__(kFiltThreads) filter_count_kernel(const float 
 // an in-block scan of its tiles' counts gives each tile's offset, and only
 // tiles with survivors are visited.  Block 0 writes the survivor count.
 template <int G, bool KEYS>
-__global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const float *__restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(kFiltThreads, 3) filter_scatter_kernel(const float *__restrict__ pts, int64_t n,
                                                                       void *ws, Layout L,
                                                                       uint32_t *__restrict__ surv_idx,
                                                                       float2 *__restrict__ surv_pts,
                                                                       uint32_t *surv_count, int allow_spec)
 {
-    __shared__ uint32_t s_off[kFiltItems / G][NW];
     __shared__ uint32_t s_abort;
     __shared__ uint32_t s_red[2][NW];
     __shared__ uint32_t s_list[kFiltThreads];    // non-empty tiles of a chunk: offset in chunk
@@ -674,48 +832,10 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
         if (tid == 0) s_nlist = nlist;
         __syncthreads();
         const uint32_t nl = s_nlist;
-        for (uint32_t li = 0; li < nl; ++li) {
-            const int64_t tile = c0 + s_list[li];
-            const uint32_t out_off = s_loff[li];
-            const int64_t base = tile * kFiltTile;
-        const uint32_t keep = bits[tile * kFiltThreads + tid];
-        // coordinates of the kept points only (the decisions are stored)
-        float px[kFiltItems], py[kFiltItems];
-        constexpr int ROWS = kFiltItems / G;
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            if constexpr (G == 2) {
-                px[2 * r] = py[2 * r] = px[2 * r + 1] = py[2 * r + 1] = 0.0f;
-                if ((keep >> (2 * r)) & 3u) {
-                    const int64_t i = base + (int64_t)(r * kFiltThreads + tid) * 2;
-                    float4 v;
-                    if (i + 1 < n) {
-                        v = __ldcs(reinterpret_cast<const float4 *>(pts) + i / 2);
-                    } else {
-                        const float2 a = reinterpret_cast<const float2 *>(pts)[i];
-                        v = make_float4(a.x, a.y, 0.0f, 0.0f);
-                    }
-                    px[2 * r] = v.x;
-                    py[2 * r] = v.y;
-                    px[2 * r + 1] = v.z;
-                    py[2 * r + 1] = v.w;
-                }
-            } else {
-                px[r] = py[r] = 0.0f;
-                if ((keep >> r) & 1u) {
-                    const float2 v = reinterpret_cast<const float2 *>(pts)[base + r * kFiltThreads + tid];
-                    px[r] = v.x;
-                    py[r] = v.y;
-                }
-            }
-        }
-            row_counts<G>(keep, s_off);
-            __syncthreads();
-            if (threadIdx.x < 32) scan_rows_warp0<G>(s_off);
-            __syncthreads();
-            scatter_tile<G, KEYS>(keep, base, out_off, s_off, px, py, surv_idx, surv_pts, out_keys, out_pay);
-            __syncthreads();
-        }
+        for (uint32_t li = warp; li < nl; li += NW)
+            scatter_tile_warp<G, KEYS>(pts, n, bits + (c0 + s_list[li]) * kFiltThreads, (c0 + s_list[li]) * kFiltTile,
+                                       s_loff[li], surv_idx, surv_pts, out_keys, out_pay);
+        __syncthreads();   // s_list, s_loff and s_red are rebuilt for the next chunk
         run += chunk_total;
     }
 }
@@ -726,11 +846,10 @@ __global__ void __launch_bounds__(kFiltThreads) filter_scatter_kernel(const floa
 // ---------------------------------------------------------------------------
 // Thread t tests points lo + r * 256 + t of the set (r < 16), below hi.
 __device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, int64_t lo, int64_t hi,
-                                                 const Octagon &so, float (&px)[kFiltItems],
+                                                 const OctSmem &so, float (&px)[kFiltItems],
                                                  float (&py)[kFiltItems], FiltQueue &fq)
 {
-    uint32_t keep = 0;
-    bool deferred = false;
+    uint32_t keep = 0, dm = 0;
 #pragma unroll
     for (int r = 0; r < kFiltItems; ++r) {
         const int64_t i = lo + r * kFiltThreads + threadIdx.x;
@@ -740,25 +859,25 @@ __device__ __forceinline__ uint32_t bx_load_test(const float2 *__restrict__ p2, 
             px[r] = v.x;
             py[r] = v.y;
             const uint32_t c = first_look<false>(so, v.x, v.y);
-            if (c == 2u) deferred = true;
-            if (c == 1u) keep |= 1u << r;
-            else if (c == 2u) defer(fq, (uint32_t)r);
+            keep |= (c == 1u ? 1u : 0u) << r;
+            dm |= (c == 2u ? 1u : 0u) << r;
         }
     }
     const uint32_t wbase = threadIdx.x & ~31u;
-    return keep | resolve_deferred<false>(fq, so, deferred, [&](uint32_t ln, uint32_t item) {
+    return keep | resolve_deferred<false>(fq, so, dm, [&](uint32_t ln, uint32_t item) {
                return p2[lo + (int64_t)item * kFiltThreads + wbase + ln];
            });
 }
 
 // Copies set b's polygon to shared memory when the block moves to a new set.
-__device__ __forceinline__ void bx_octagon_to_smem(Octagon &so, int64_t &cur, int64_t b, const Octagon *octs)
+__device__ __forceinline__ void bx_octagon_to_smem(OctSmem &so, int64_t &cur, int64_t b, const Octagon *octs)
 {
     if (b == cur) return;   // block-uniform
     __syncthreads();
     const uint32_t *src = reinterpret_cast<const uint32_t *>(octs + b);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(&so);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(static_cast<Octagon *>(&so));
     for (uint32_t w = threadIdx.x; w < sizeof(Octagon) / 4; w += blockDim.x) dst[w] = src[w];
+    pack_edges(so, octs[b]);
     __syncthreads();
     cur = b;
 }
@@ -766,57 +885,61 @@ __device__ __forceinline__ void bx_octagon_to_smem(Octagon &so, int64_t &cur, in
 __global__ void __launch_bounds__(kFiltThreads) bx_filter_count_kernel(const float *__restrict__ pts, void *ws,
                                                                        Layout L, BatchLayout BL)
 {
-    __shared__ Octagon so;
+    __shared__ OctSmem so;
     __shared__ FiltQueue s_fq[NW];
+    __shared__ uint32_t s_cnt[kCountRing];
     queue_reset(s_fq[threadIdx.x >> 5]);
-    __shared__ uint32_t s_w[NW];
     const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
     if (bc->abort) return;
+    for (int i = threadIdx.x; i < kCountRing; i += kFiltThreads) s_cnt[i] = 0u;   // (the first set's load syncs)
     const SetInfo *sets = at<SetInfo>(ws, BL.sets);
     const uint32_t *tile_set = at<uint32_t>(ws, BL.tile_set);
     const Octagon *octs = at<Octagon>(ws, BL.octs);
     unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
     uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
     uint32_t *soct = at<uint32_t>(ws, BL.soct);
-    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t lane = lane_id();
     // a contiguous range of tiles per block: the polygon is loaded once per
-    // set the range touches
+    // set the range touches (a block-wide step; between two, the warps run
+    // free and add their tile counts up in s_cnt)
     const int64_t T = bc->tiles;
     const int64_t per = ceil_div(T, (int64_t)gridDim.x);
     const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(T, t0 + per);
     int64_t cur = -1;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int64_t b = tile_set[t];
-        bx_octagon_to_smem(so, cur, b, octs);
-        if (threadIdx.x == 0 && t + 1 < t1) {   // the next tile streams into L2 meanwhile
-            const int64_t nb = tile_set[t + 1];
-            const int64_t nlo = (t + 1 - sets[nb].tile_base) * (int64_t)kFiltTile;
-            const int64_t nhi = min(nlo + kFiltTile, sets[nb].n);
-            const float2 *np = reinterpret_cast<const float2 *>(pts) + sets[nb].pt_begin;
-            const uintptr_t a0 = (reinterpret_cast<uintptr_t>(np + nlo) + 15) & ~(uintptr_t)15;
-            const uintptr_t a1 = reinterpret_cast<uintptr_t>(np + nhi) & ~(uintptr_t)15;
-            if (a1 > a0) bulk_prefetch_l2(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
-        }
-        uint32_t keep = 0;
-        if (!so.abort) {
-            const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
-            const int64_t hi = min(lo + kFiltTile, sets[b].n);
-            float px[kFiltItems], py[kFiltItems];
-            keep = bx_load_test(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, lo, hi, so, px, py,
-                                s_fq[threadIdx.x >> 5]);
-        }
-        bits[(size_t)t * kFiltThreads + threadIdx.x] = (uint16_t)keep;
-        uint32_t c = __popc(keep);
+    for (int64_t w0 = t0; w0 < t1; w0 += kCountRing) {
+        const int64_t w1 = min(t1, w0 + kCountRing);
+        for (int64_t t = w0; t < w1; ++t) {
+            const int64_t b = tile_set[t];
+            bx_octagon_to_smem(so, cur, b, octs);
+            if (threadIdx.x == 0 && t + 1 < t1) {   // the next tile streams into L2 meanwhile
+                const int64_t nb = tile_set[t + 1];
+                const int64_t nlo = (t + 1 - sets[nb].tile_base) * (int64_t)kFiltTile;
+                const int64_t nhi = min(nlo + kFiltTile, sets[nb].n);
+                const float2 *np = reinterpret_cast<const float2 *>(pts) + sets[nb].pt_begin;
+                const uintptr_t a0 = (reinterpret_cast<uintptr_t>(np + nlo) + 15) & ~(uintptr_t)15;
+                const uintptr_t a1 = reinterpret_cast<uintptr_t>(np + nhi) & ~(uintptr_t)15;
+                if (a1 > a0) bulk_prefetch_l2(reinterpret_cast<const void *>(a0), (uint32_t)(a1 - a0));
+            }
+            uint32_t keep = 0;
+            if (!so.abort) {
+                const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
+                const int64_t hi = min(lo + kFiltTile, sets[b].n);
+                float px[kFiltItems], py[kFiltItems];
+                keep = bx_load_test(reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin, lo, hi, so, px, py,
+                                    s_fq[threadIdx.x >> 5]);
+            }
+            bits[(size_t)t * kFiltThreads + threadIdx.x] = (uint16_t)keep;
+            uint32_t c = __popc(keep);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) s_w[warp] = c;
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0 && c) atomicAdd(&s_cnt[t - w0], c);
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t sum = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) sum += s_w[w];
-            status[t] = sum;
-            if (sum) atomicAdd(&soct[b], sum);
+        for (int64_t i = threadIdx.x; i < w1 - w0; i += kFiltThreads) {
+            const uint32_t v = s_cnt[i];
+            status[w0 + i] = v;
+            s_cnt[i] = 0u;
+            if (v) atomicAdd(&soct[tile_set[w0 + i]], v);
         }
         __syncthreads();
     }
@@ -918,10 +1041,11 @@ __global__ void __launch_bounds__(1024) bx_filter_scan_kernel(void *ws, Layout L
     if (threadIdx.x == 0) bc->nsc = (uint32_t)tsc;
 }
 
-__global__ void __launch_bounds__(kFiltThreads) bx_filter_scatter_kernel(const float *__restrict__ pts, void *ws,
-                                                                         Layout L, BatchLayout BL)
+// One warp per tile with survivors (warps of the whole grid in turn); the
+// scan left each tile's output offset in the high half of filt_status.
+__global__ void __launch_bounds__(kFiltThreads, 3) bx_filter_scatter_kernel(const float *__restrict__ pts, void *ws,
+                                                                            Layout L, BatchLayout BL)
 {
-    __shared__ uint32_t s_off[kFiltItems][NW];
     const BatchCtrl *bc = at<BatchCtrl>(ws, BL.bctrl);
     if (bc->abort) return;
     const SetInfo *sets = at<SetInfo>(ws, BL.sets);
@@ -931,29 +1055,15 @@ __global__ void __launch_bounds__(kFiltThreads) bx_filter_scatter_kernel(const f
     uint32_t *out_keys = at<uint32_t>(ws, L.keys[0]);
     unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[0]);
     const uint32_t T = bc->tiles;
-    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+    const uint32_t nwarps = gridDim.x * NW;
+    for (uint32_t t = blockIdx.x * NW + (threadIdx.x >> 5); t < T; t += nwarps) {
         const unsigned long long st = status[t];
-        if ((st & 0xffffffffull) == 0) continue;   // block-uniform
+        if ((st & 0xffffffffull) == 0) continue;   // warp-uniform
         const int64_t b = tile_set[t];
         const int64_t lo = (int64_t)(t - sets[b].tile_base) * kFiltTile;
-        const uint32_t keep = bits[(size_t)t * kFiltThreads + threadIdx.x];
-        const float2 *p2 = reinterpret_cast<const float2 *>(pts) + sets[b].pt_begin;
-        float px[kFiltItems], py[kFiltItems];
-#pragma unroll
-        for (int r = 0; r < kFiltItems; ++r) {
-            px[r] = py[r] = 0.0f;
-            if ((keep >> r) & 1u) {
-                const float2 v = p2[lo + r * kFiltThreads + threadIdx.x];
-                px[r] = v.x;
-                py[r] = v.y;
-            }
-        }
-        row_counts<1>(keep, s_off);
-        __syncthreads();
-        if (threadIdx.x < 32) scan_rows_warp0<1>(s_off);
-        __syncthreads();
-        scatter_tile<1, true>(keep, lo, st >> 32, s_off, px, py, nullptr, nullptr, out_keys, out_pay);
-        __syncthreads();
+        const float *p = pts + 2 * sets[b].pt_begin;
+        scatter_tile_warp<1, true>(p, sets[b].n, bits + (size_t)t * kFiltThreads, lo, (uint32_t)(st >> 32), nullptr,
+                                   nullptr, out_keys, out_pay);
     }
 }
 
@@ -988,11 +1098,13 @@ template <int G, bool KEYS, bool BOX>
 cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *surv_idx,
                             float *surv_pts, uint32_t *surv_count, cudaStream_t st, bool fan, const KgonStage *kg)
 {
-    static int per_sm_c = occupancy(filter_count_kernel<G, BOX>, kFiltThreads);
+    // both passes use the same grid (block b owns the same tile range),
+    // the count pass's resident blocks (the scatter pass's warps take
+    // tiles on their own, so a second partial wave of it costs little)
+    static const int per_sm = occupancy(filter_count_kernel<G, BOX>, kFiltThreads);
     const int64_t ntiles = ceil_div(n, kFiltTile);
-    // both passes use the same grid: block b owns the same tile range
     const int64_t bc = std::max<int64_t>(
-        1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm_c, kFiltMaxBlocks), ntiles));
+        1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm, kFiltMaxBlocks), ntiles));
     filter_count_kernel<G, BOX><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
     if (kg && (kg->kdev || kg->K != 8)) {   // the second polygon, over the octagon's survivors
         probe_after(CH_K_FILTER, st);

@@ -89,14 +89,20 @@ __device__ __forceinline__ int prev_bin(int b) { return b == 0 ? kFanBins - 1 : 
 // thread's items interleave): 1 inside, 0 outside, 2 undecided (a sign the
 // binary32 bound does not prove, and that matters); fan_inside_exact
 // settles the undecided ones.
+// The two signs with c as a vertex are taken with c as the reference point
+// (a cyclic shift of a triple keeps its orientation): orient(c, v, p) as
+// orient(v, p, c) and orient(w, c, p) as orient(p, w, c), so that both use
+// the differences p - c of the bin; orient_f32 certifies the sign of either
+// form with the same bound.
 __device__ __forceinline__ int fan_signs_f32(const float2 *V, float cx, float cy, float px, float py)
 {
-    const int b = fan_bin(px - cx, py - cy);
+    const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy);
+    const int b = fan_bin(dx, dy);
     const float2 v = V[b];
-    const int o = orient_f32(cx, cy, v.x, v.y, px, py);
+    const int o = orient_f32_ref(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), dx, dy);          // (v, p, c)
     const float2 w = V[o == 1 ? next_bin(b) : prev_bin(b)];
     const int e1 = orient_f32(v.x, v.y, w.x, w.y, px, py);
-    const int e2 = orient_f32(w.x, w.y, cx, cy, px, py);
+    const int e2 = orient_f32_ref(dx, dy, __fsub_rn(w.x, cx), __fsub_rn(w.y, cy));         // (p, w, c)
     const bool out = (e1 != 2 && e1 != o) || (e2 != 2 && e2 != o);
     return o == 2 ? 2 : (out ? 0 : (e1 == o && e2 == o ? 1 : 2));
 }
@@ -155,22 +161,24 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     const int64_t ntiles = ceil_div(n, FTILE);
     const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(4, ntiles / kBinTiles));   // every stride-th tile
     const int64_t nsamp = ceil_div(ntiles, stride);
-    for (int64_t k = blockIdx.x; k < nsamp; k += gridDim.x) {
-        const int64_t base = k * stride * FTILE;
-        if (threadIdx.x == 0 && k + gridDim.x < nsamp) {   // this block's next sample tile streams into L2
-            const int64_t nb = (k + gridDim.x) * stride * FTILE;
+    // two sample tiles per trip (k and k + grid: twice the loads in flight
+    // of one 512-thread block per SM); the next two stream into L2 meanwhile
+    const int64_t g = gridDim.x;
+    for (int64_t k = blockIdx.x; k < nsamp; k += 2 * g) {
+        if (threadIdx.x < 2 && k + (2 + threadIdx.x) * g < nsamp) {
+            const int64_t nb = (k + (2 + threadIdx.x) * g) * stride * FTILE;
             const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, n - nb);
             if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
         }
-        float2 p[FITEMS];
+        float2 p[2 * FITEMS];
 #pragma unroll
-        for (int r = 0; r < FITEMS; ++r) {
-            const int64_t q = base + r * FT + threadIdx.x;
+        for (int r = 0; r < 2 * FITEMS; ++r) {
+            const int64_t q = (k + (r / FITEMS) * g) * stride * FTILE + (r % FITEMS) * FT + threadIdx.x;
             p[r] = q < n ? input_point(pts, q) : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
-        for (int r = 0; r < FITEMS; ++r) {
-            const int64_t q = base + r * FT + threadIdx.x;
+        for (int r = 0; r < 2 * FITEMS; ++r) {
+            const int64_t q = (k + (r / FITEMS) * g) * stride * FTILE + (r % FITEMS) * FT + threadIdx.x;
             if (q < n) {
                 const float dx = p[r].x - cx, dy = p[r].y - cy;
                 const int b = fan_bin(dx, dy);

@@ -4,9 +4,11 @@ the points it cannot prove strictly inside P0 as candidates, and when its
 last block proves P0 inside the final octagon the filter tests only the
 candidates.  Through ch_extremes_filter (vertices and survivor lists) and
 ch_hull (hulls), element by element against the oracle, both when the
-speculation serves the filter and when it falls back: a candidate segment
-that overflows (the unit circle: nothing is inside), a sample vertex
-outside the final octagon (planted), and the single-pass schedule."""
+speculation serves the filter and when it falls back: a probe of evenly
+spaced points that predicts an overflow (the unit circle: nothing is
+inside), a candidate segment that overflows although the probe passed, a
+sample vertex outside the final octagon (planted), and the single-pass
+schedule."""
 import numpy as np
 import pytest
 import torch
@@ -97,8 +99,27 @@ def test_normal_sample_octagon_outside_falls_back():
 
 
 def test_circle_falls_back():
-    # no point is inside any octagon of circle points: the segments overflow
+    # no point is inside any octagon of circle points: the probe sees them
+    # all outside the sample's region and the sweep does not speculate
     p = pointgen.make_points("circle", N, seed=6)
+    got = run(p)
+    check(p, got)
+    assert got[4] == 0
+
+
+def test_segment_overflow_after_the_probe_passed():
+    # normal points at the probe's indices (k * (N // 1024)) and in the 32
+    # sample runs, every other point on a circle of radius 6, outside the
+    # sample's region (about 0.9 of the sample extremes, near 4): the probe
+    # finds nothing outside, the sweep's candidate segments overflow
+    p = pointgen.make_points("normal", N, seed=10)
+    keep = np.zeros(N, bool)
+    keep[np.arange(1024) * (N // 1024)] = True
+    for b in range(32):
+        s0 = (N - 2048) * b // 31
+        keep[s0:s0 + 2048] = True
+    ring = pointgen.make_points("circle", N, seed=11).astype(np.float64) * 6.0
+    p[~keep] = ring[~keep].astype(np.float32)
     got = run(p)
     check(p, got)
     assert got[4] == 0
