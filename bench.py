@@ -214,20 +214,31 @@ def load_traffic(kernel):
         return None
 
 
-def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev):
+def fan_rates(tr, dist):
+    """(warp instructions, DRAM bytes per algorithmic byte) per octagon
+    survivor of the fan kernels for a set of distribution `dist`: the
+    capture of that distribution when the record has one, else its
+    default."""
+    rec = (tr.get("per_dist") or {}).get(dist) or tr
+    return rec["warp_inst_per_survivor"], rec["dram_per_algorithmic_byte"]
+
+
+def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev, dists=None):
     """Roofline of the fan kernels, which are bound by instruction issue,
     not by HBM: warp instructions issued per second against the SMs' issue
     rate (4 warp schedulers per SM, one warp instruction each per clock, at
     the highest SM clock seen).  The instructions per octagon survivor come
-    from an ncu capture (profiles/traffic.json, void once kgon.cu changed);
-    the time is the event time of the timed launches."""
+    from ncu captures (profiles/traffic.json, per distribution of the
+    set, void once kgon.cu changed); the time is the event time of the
+    timed launches."""
     import torch
 
     tr = load_traffic("kgon")
     if not tr or "warp_inst_per_survivor" not in tr:
         return None
-    fan_s = sum(s for s, t in zip(s_list, t_list) if t < s)   # sets whose fan pass ran
-    inst = tr["warp_inst_per_survivor"] * fan_s * steps
+    dists = dists or [None] * len(s_list)
+    fan = [(s, d) for s, t, d in zip(s_list, t_list, dists) if t < s]   # sets whose fan pass ran
+    inst = sum(fan_rates(tr, d)[0] * s for s, d in fan) * steps
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_max_mhz") or 2070.0
     peak = sms * 4 * mhz * 1e6 / 1e12                          # T warp-instructions/s
@@ -242,7 +253,7 @@ def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev):
             # (8 B per octagon survivor tested) over the event time
             "hbm_achieved_gbs": round(hbm_gbs, 1), "hbm_peak_gbs": hbm_peak,
             "hbm_frac": round(hbm_gbs / hbm_peak, 4), "hbm_peak_source": hbm_kind,
-            "traffic": int(tr["dram_per_algorithmic_byte"] * per_launch_bytes),
+            "traffic": int(sum(fan_rates(tr, d)[1] * 8 * s for s, d in fan) * steps / dom_launches),
             "traffic_source": tr["capture"], "algorithmic_bytes_per_launch": int(per_launch_bytes),
             "warp_instr_per_launch": int(inst / dom_launches), "avg_launch_ms": round(dom_ms / dom_launches, 4)}
 
@@ -377,7 +388,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     roof = None
     if dom_launches and dominant == "kgon":
-        roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev)
+        roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev, list(DISTS))
     if dom_launches and roof is None:
         per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts)
         if per_step_bytes is not None:

@@ -56,6 +56,22 @@ def test_alu_roofline_counts_fan_sets_only(one_device, monkeypatch):
     assert r["hbm_frac"] == pytest.approx(gbs / hbm_peak, abs=1e-3)
 
 
+def test_alu_roofline_takes_each_distributions_capture(one_device, monkeypatch):
+    rec = dict(FAN_RECORD, per_dist={"circle": {"warp_inst_per_survivor": 5.0, "dram_per_algorithmic_byte": 1.3},
+                                     "displaced": {"warp_inst_per_survivor": 3.0, "dram_per_algorithmic_byte": 1.4}})
+    monkeypatch.setattr(bench, "load_traffic", lambda kernel: rec if kernel == "kgon" else None)
+    steps, launches, ms = 5, 60, 6.0
+    r = bench.alu_roofline(ms, launches, steps, N, S, T, {"sm_max_mhz": 2070.0}, None,
+                           ["normal", "circle", "displaced"])
+    inst = (5.0 * S[1] + 3.0 * S[2]) * steps
+    assert r["warp_instr_per_launch"] == int(inst / launches)
+    assert r["traffic"] == int((1.3 * 8 * S[1] + 1.4 * 8 * S[2]) * steps / launches)
+    # a distribution without its own capture takes the default
+    r2 = bench.alu_roofline(ms, launches, steps, N, S, T, {"sm_max_mhz": 2070.0}, None,
+                            ["normal", "circle", "gaussians"])
+    assert r2["warp_instr_per_launch"] == int((5.0 * S[1] + 4.5 * S[2]) * steps / launches)
+
+
 def test_alu_roofline_void_when_source_changed(one_device, monkeypatch):
     rec = copy.deepcopy(json.load(open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json"))))
     rec["kgon"]["source_sha"] = "0" * 16
