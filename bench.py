@@ -168,20 +168,26 @@ class ClockSampler:
 SMALL_HULL = 512   # at most this many points to sort: one block sorts and chains them (no sort passes)
 
 
-def algorithmic_bytes(kernel, n, s_list, t_list):
+def algorithmic_bytes(kernel, n, s_list, t_list, f_list=None):
     """Bytes a kernel must move in one step (all its launches for the step's
     sets), from the data it reads and writes by definition; s_list holds the
     octagon-filter survivors of each set, t_list the points the hull step
-    sorts (the survivors of the fan test as well, when it ran).  Sets with
-    at most SMALL_HULL points to sort run no sort and chain kernels."""
+    sorts (the survivors of the fan test as well, when it ran), f_list the
+    points left by the fan's first level (t_list when absent: no second
+    level).  Sets with at most SMALL_HULL points to sort run no sort and
+    chain kernels."""
+    f_list = t_list if f_list is None else f_list
     if kernel == "extremes":
         return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
-        return sum(8 * n + 12 * t for t in t_list)          # read points, write key + payload per point kept
+        return sum(8 * n + 12 * f for f in f_list)          # read points, write key + payload per point kept
     if kernel == "kgon":
         # the fan test of the octagon survivors when it ran (read their
-        # coordinates); otherwise only samples
-        return sum(8 * s if t < s else 0 for s, t in zip(s_list, t_list))
+        # coordinates); otherwise only samples.  The second level reads the
+        # first level's survivors twice (sub-bin maxima, test: key +
+        # payload) and copies the points it keeps
+        return sum((8 * s if f < s else 0) + (24 * f + 24 * t if t < f else 0)
+                   for s, t, f in zip(s_list, t_list, f_list))
     big = [t for t in t_list if t > SMALL_HULL]
     if kernel == "sort_hist":
         return sum(4 * t for t in big)                      # read the 32-bit keys
@@ -223,7 +229,7 @@ def fan_rates(tr, dist):
     return rec["warp_inst_per_survivor"], rec["dram_per_algorithmic_byte"]
 
 
-def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev, dists=None):
+def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev, dists=None, f_list=None):
     """Roofline of the fan kernels, which are bound by instruction issue,
     not by HBM: warp instructions issued per second against the SMs' issue
     rate (4 warp schedulers per SM, one warp instruction each per clock, at
@@ -237,13 +243,14 @@ def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev, dists
     if not tr or "warp_inst_per_survivor" not in tr:
         return None
     dists = dists or [None] * len(s_list)
-    fan = [(s, d) for s, t, d in zip(s_list, t_list, dists) if t < s]   # sets whose fan pass ran
+    f_list = t_list if f_list is None else f_list
+    fan = [(s, d) for s, f, d in zip(s_list, f_list, dists) if f < s]   # sets whose fan pass ran
     inst = sum(fan_rates(tr, d)[0] * s for s, d in fan) * steps
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_max_mhz") or 2070.0
     peak = sms * 4 * mhz * 1e6 / 1e12                          # T warp-instructions/s
     achieved = inst / (dom_ms * 1e-3) / 1e12
-    per_launch_bytes = algorithmic_bytes("kgon", n, s_list, t_list) * steps / dom_launches
+    per_launch_bytes = algorithmic_bytes("kgon", n, s_list, t_list, f_list) * steps / dom_launches
     hbm_peak, hbm_kind = peaks()
     hbm_gbs = per_launch_bytes / (dom_ms / dom_launches * 1e-3) / 1e9
     return {"kernel": "kgon", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
@@ -344,7 +351,7 @@ def run_ours(args):
     # one probed step, set by set: event time of every kernel
     per_set = {}
     probe_all = {k: (0.0, 0) for k in KERNEL_IDS}
-    surv, sorted_pts, spec = [], [], []
+    surv, sorted_pts, spec, fan1 = [], [], [], []
     for k in range(len(DISTS)):
         ch.ch_probe_start(KERNEL_IDS, max_launches=64)
         ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
@@ -355,6 +362,7 @@ def run_ours(args):
         surv.append(c[0])
         sorted_pts.append(c[1])
         spec.append(c[2])
+        fan1.append(c[3])
     ws.check()
     dominant = max(probe_all, key=lambda k: probe_all[k][0])
     total_probe = sum(v[0] for v in probe_all.values())
@@ -388,9 +396,9 @@ def run_ours(args):
     peak, peak_kind = peaks()
     roof = None
     if dom_launches and dominant == "kgon":
-        roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev, list(DISTS))
+        roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev, list(DISTS), fan1)
     if dom_launches and roof is None:
-        per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts)
+        per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts, fan1)
         if per_step_bytes is not None:
             # algorithmic bytes of all timed launches over their summed event
             # time (= per-launch bytes over the average launch duration)
@@ -408,7 +416,7 @@ def run_ours(args):
     filt = None
     if probe_all["filter"][1]:
         fms = probe_all["filter"][0]
-        fb = algorithmic_bytes("filter", n, surv, sorted_pts)
+        fb = algorithmic_bytes("filter", n, surv, sorted_pts, fan1)
         filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / len(DISTS), 4),
                 "gbs": round(fb / (fms * 1e-3) / 1e9, 1), "frac_of_peak": round(fb / (fms * 1e-3) / 1e9 / peak, 4)}
 
@@ -489,6 +497,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
                        "survivors": dict(zip(DISTS, surv)), "sorted": dict(zip(DISTS, sorted_pts)),
                        "speculative_sweep": dict(zip(DISTS, spec)),
+                       "fan_first_level": dict(zip(DISTS, fan1)),
                        "hull_sizes": dict(zip(DISTS, hull_sizes))},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roof, "filter": filt, "kernel_shares": shares, "kernel_ms_per_set": per_set,

@@ -217,7 +217,10 @@ typedef enum {
     CH_TUNE_BX_FAN_CHUNK = 5,   /* tiles per work item of the fan refine: 8, 16, 32 or 64 (default 64) */
     CH_TUNE_BX_EXT_ITEMS = 6,   /* points per thread per 4096-point tile of the extremes sweep:
                                    4, 8 or 16, i.e. blocks of 1024, 512 or 256 threads (default 16) */
-    CH_TUNE_COUNT = 7
+    CH_TUNE_FAN2_MIN_LOG2 = 7,  /* single-set hull step: the fan's second level runs when the first
+                                   leaves at least 2^value points, 10..31 (default 19); sets of
+                                   fewer than 2^19 points have no second level */
+    CH_TUNE_COUNT = 8
 } ch_tune_knob;
 ch_status ch_tune_set(int32_t knob, int32_t value);
 ch_status ch_tune_get(int32_t knob, int32_t *value);
@@ -323,8 +326,11 @@ ch_status ch_probe_start(uint32_t kernel_mask, int32_t max_launches);
  * around the bounding-box centre removed some), counts[2] = 1 when the
  * speculative single sweep served the filter (the extremes sweep proved
  * every point but its candidates strictly inside the octagon, so the
- * filter read only the candidates), else 0.  counts holds 3 entries.
- * Instrumentation; CH_ERR_ARG / CH_ERR_CAPACITY as for ch_hull. */
+ * filter read only the candidates), else 0, counts[3] = points left by the
+ * fan's first level (the input of its second level over the survivors,
+ * with kFan2Sub times as many bins, when that ran; else counts[1]).
+ * counts holds 4 entries.  Instrumentation; CH_ERR_ARG / CH_ERR_CAPACITY
+ * as for ch_hull. */
 ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32_t *counts, void *stream);
 
 /* Stop timing: waits for the recorded events, writes per kernel id the summed

@@ -35,7 +35,8 @@ SYMBOLS = ("ch_workspace_size", "ch_workspace_init", "ch_extremes", "ch_filter",
            "ch_filter_variant", "ch_hull_counts", "ch_filter_kgon", "ch_hull_kgon", "ch_kgon_features",
            "ch_mlp_forward", "ch_mlp_train_step", "ch_mlp_param_count", "ch_mlp_scratch_floats",
            "ch_tune_set", "ch_tune_get", "ch_hull_octagon_kgon", "ch_hull_learned")
-TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit", "bx_fan_stride", "bx_fan_chunk", "bx_ext_items")
+TUNE_KNOBS = ("bx_extremes", "bx_filter", "bx_sort_pass", "bx_emit", "bx_fan_stride", "bx_fan_chunk", "bx_ext_items",
+              "fan2_min_log2")
 # ch_filter_noalloc reports a device-side error as this bit | the status code in its count
 NOALLOC_FAILED = 0x80000000
 KERNELS = ("extremes", "octagon", "filter", "sort_hist", "sort_pass", "chain", "emit", "finish", "kgon")
@@ -202,9 +203,11 @@ def ch_hull_batched(pts, offsets, hull_idx, hull_offsets, ws, stream=None):
                                   _ptr(ws, "ws"), ws.numel(), _stream(stream)), "ch_hull_batched")
 
 
-def ch_tune_set(knob: str, blocks_per_sm: int):
-    """Blocks per SM of a batched kernel's grid (0: the built-in choice)."""
-    _check(load().ch_tune_set(TUNE_KNOBS.index(knob), int(blocks_per_sm)), "ch_tune_set")
+def ch_tune_set(knob: str, value: int):
+    """A tuning knob (convhull.h's ch_tune_knob, by name): a batched
+    kernel's blocks per SM or launch shape, or the second fan level's
+    threshold; 0 restores the built-in choice."""
+    _check(load().ch_tune_set(TUNE_KNOBS.index(knob), int(value)), "ch_tune_set")
 
 
 def ch_tune_get(knob: str) -> int:
@@ -214,13 +217,13 @@ def ch_tune_get(knob: str) -> int:
 
 
 def ch_hull_counts(ws, n, stream=None):
-    """(octagon survivors, points sorted, speculative sweep used: 0/1) of the
-    last ch_hull call for n points on ws (instrumentation; synchronises the
-    stream)."""
-    out = (ctypes.c_uint32 * 3)()
+    """(octagon survivors, points sorted, speculative sweep used: 0/1, points
+    left by the fan's first level) of the last ch_hull call for n points on
+    ws (instrumentation; synchronises the stream)."""
+    out = (ctypes.c_uint32 * 4)()
     _check(load().ch_hull_counts(_ptr(ws, "ws"), ws.numel(), int(n), ctypes.addressof(out), _stream(stream)),
            "ch_hull_counts")
-    return int(out[0]), int(out[1]), int(out[2])
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
 def ch_last_error(ws, stream=None) -> int:

@@ -67,7 +67,7 @@ def tune(pts, offsets, ws, reps: int = 3, rounds: int = 1) -> dict:
     best_ms = t_default = time_batched(pts, offsets, idx, hoff, ws, reps)
     for _ in range(rounds):
         for k in TUNE_KNOBS:
-            for v in CANDIDATES[k]:
+            for v in CANDIDATES.get(k, ()):   # (knobs of the single-set call are not the batch's)
                 trial = dict(best, **{k: v})
                 apply(trial)
                 t = time_batched(pts, offsets, idx, hoff, ws, reps)

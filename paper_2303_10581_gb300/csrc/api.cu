@@ -48,6 +48,7 @@ extern "C" ch_status ch_tune_set(int32_t knob, int32_t value)
     if (knob == CH_TUNE_BX_FAN_CHUNK && value && value != 8 && value != 16 && value != 32 && value != 64)
         return CH_ERR_ARG;
     if (knob == CH_TUNE_BX_EXT_ITEMS && value && value != 4 && value != 8 && value != 16) return CH_ERR_ARG;
+    if (knob == CH_TUNE_FAN2_MIN_LOG2 && value && (value < 10 || value > 31)) return CH_ERR_ARG;
     ch::g_tune[knob].store(value, std::memory_order_relaxed);
     return CH_OK;
 }
@@ -63,8 +64,10 @@ extern "C" ch_status ch_workspace_size(int64_t n, int64_t num_sets, size_t *byte
 {
     if (!bytes || n < 0 || num_sets < 1) return CH_ERR_ARG;
     if (n > kMaxN) return CH_ERR_CAPACITY;
-    // the batched layout holds the single-set one as a prefix
-    *bytes = batched_bytes(n, num_sets);
+    // room for either layout: the single-set one (ch_hull and the filters:
+    // it has the second fan level's tables from kFan2MinN points) and the
+    // batched one for num_sets sets
+    *bytes = std::max(make_layout(n).total, batched_bytes(n, num_sets));
     return CH_OK;
 }
 
@@ -292,13 +295,16 @@ extern "C" ch_status ch_hull_counts(void *ws, size_t ws_bytes, int64_t n, uint32
     if (ch_status s = check_ws(ws, ws_bytes, L)) return s;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return CH_ERR_CUDA;
     uint32_t sorted = 0, s_oct = 0, spec = 0;
+    Fan2Ctrl f2{};
     if (cudaMemcpy(&sorted, &at<Ctrl>(ws, L.ctrl)->surv_count, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&s_oct, &at<KgonCtrl>(ws, L.kgon_ctrl)->s_oct, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&spec, &at<Octagon>(ws, L.oct)->spec, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(&spec, &at<Octagon>(ws, L.oct)->spec, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&f2, at<Fan2Ctrl>(ws, L.fan2), sizeof f2, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CH_ERR_CUDA;
     counts[0] = s_oct ? s_oct : sorted;
     counts[1] = sorted;
     counts[2] = spec;
+    counts[3] = f2.on ? f2.count_in : sorted;
     return CH_OK;
 }
 

@@ -88,9 +88,23 @@ struct ExtCtrl {
 constexpr int kFanBins = 28672;
 
 struct KgonCtrl {                          // zeroed with the control block
-    unsigned long long slot[kFanBins];     // packed (r^2 bits << 32 | ~index): farthest sampled input point per bin
+    unsigned long long slot[kFanBins];     // packed (far_key << 32 | ~index): farthest sampled input point per bin
     uint32_t sample, inside;               // the estimate's sample and how much of it is inside the fan
     uint32_t s_oct;                        // octagon survivors (0: the fan kernels did not run)
+    uint32_t pad;
+};
+
+// second fan level (kgon.cu): over the first level's survivors, kFan2Sub
+// sub-bins per bin, each vertex the farthest survivor of its sub-bin
+constexpr int kFan2Sub = 8;
+constexpr int kFan2Bins = kFanBins * kFan2Sub;   // 229376
+constexpr uint32_t kFan2MinS = 1u << 19;         // fewer survivors of the first level: the sort takes them
+constexpr int64_t kFan2MinN = 1 << 19;           // smaller sets get no tables
+
+struct Fan2Ctrl {                          // zeroed with the control block
+    uint32_t on;                           // 1: the second level runs this call
+    uint32_t count_in;                     // survivors of the first level, its input
+    uint32_t bad;                          // 1: no vertices (nothing is dropped)
     uint32_t pad;
 };
 
@@ -195,6 +209,8 @@ struct Layout {
     size_t ctrl;            // Ctrl, immediately followed by
     size_t filt_status;     // u64[filt_tiles],
     size_t kgon_ctrl;       // KgonCtrl,
+    size_t fan2;            // Fan2Ctrl,
+    size_t fan2_slot;       // u64[fan2_bins]: per sub-bin the farthest survivor (far_key << 32 | ~position),
     size_t node_cnt;        // u32[n_nodes]: arrivals per merge-tree node, and
     size_t emit_status[2];  // u64[emit_tiles]: look-back of the chain compaction
     size_t zero_words;      // u64 words from ctrl to the end of emit_status[1]
@@ -211,8 +227,10 @@ struct Layout {
     size_t utmp;          // u32[n]
     size_t spec, p0;        // SpecCtrl, the speculative sweep's test region (SpecBox, extremes.cu)
     size_t learn;           // the learned proposal's scratch (LearnScratch)
+    size_t fan2_v;          // float2[fan2_bins]: the second fan level's vertices
     size_t total;
     int64_t n, filt_tiles, sort_tiles, n_chunks, n_nodes, emit_tiles;
+    int64_t fan2_bins;      // kFan2Bins for sets of at least kFan2MinN points, else 0 (no second level)
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -320,6 +338,9 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.ctrl = take(sizeof(Ctrl));
     L.filt_status = take((size_t)L.filt_tiles * 8);
     L.kgon_ctrl = take(sizeof(KgonCtrl));
+    L.fan2_bins = (sets == 0 && n >= kFan2MinN) ? kFan2Bins : 0;
+    L.fan2 = take(sizeof(Fan2Ctrl));
+    L.fan2_slot = take((size_t)L.fan2_bins * 8);
     L.node_cnt = take((size_t)L.n_nodes * 4);
     L.emit_status[0] = take((size_t)L.emit_tiles * 8);
     L.emit_status[1] = take((size_t)L.emit_tiles * 8);
@@ -343,6 +364,7 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     L.spec = take(sizeof(SpecCtrl));
     L.p0 = take(256);
     L.learn = take(sizeof(LearnScratch));
+    L.fan2_v = take((size_t)L.fan2_bins * 8);
     L.total = o;
     return L;
 }

@@ -1121,6 +1121,12 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     filter_scatter_kernel<G, KEYS><<<(unsigned)bc, kFiltThreads, 0, st>>>(
         pts, n, ws, L, surv_idx, reinterpret_cast<float2 *>(surv_pts), surv_count, BOX ? 0 : 1);
     note_kernels(CH_K_FILTER, 2);
+    if (fan && KEYS) {   // the hull step: the fan's second level over the survivors just written
+        probe_after(CH_K_FILTER, st);
+        const cudaError_t e = launch_fan2(n, ws, L, st);
+        if (e != cudaSuccess) return e;
+        probe_before(CH_K_FILTER, st);
+    }
     return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@
 // scatter writes only the points that survive both tests:
 //
 //  fan_bins_kernel      octagon survivor count; per bin, the farthest sampled
-//                       input point (atomicMax of (r^2 bits << 32 | ~index),
+//                       input point (atomicMax of (far_key << 32 | ~index),
 //                       in shared memory per block, then in global memory)
 //  fan_build_kernel     exact centre check against the octagon; the vertex
 //                       of every bin
@@ -63,6 +63,7 @@ __device__ __forceinline__ float2 input_point(const float *pts, int64_t i)
 // the angle counter-clockwise from +x, scaled to the bins.  Any value is
 // safe (it only picks a triangle); the conversion saturates and the result
 // is clamped.
+template <int NB = kFanBins>
 __device__ __forceinline__ int fan_bin(float dx, float dy)
 {
     const float s = fabsf(dx) + fabsf(dy);
@@ -71,12 +72,61 @@ __device__ __forceinline__ int fan_bin(float dx, float dy)
         const float t = __fdividef(dy, s);
         a = dx >= 0.0f ? (dy >= 0.0f ? t : 4.0f + t) : 2.0f - t;
     }
-    const int b = __float2int_rz(a * (kFanBins / 4.0f));
-    return b < 0 ? 0 : (b >= kFanBins ? kFanBins - 1 : b);
+    const int b = __float2int_rz(a * (NB / 4.0f));
+    return b < 0 ? 0 : (b >= NB ? NB - 1 : b);
 }
 
-__device__ __forceinline__ int next_bin(int b) { return b + 1 == kFanBins ? 0 : b + 1; }
-__device__ __forceinline__ int prev_bin(int b) { return b == 0 ? kFanBins - 1 : b - 1; }
+template <int NB = kFanBins>
+__device__ __forceinline__ int next_bin(int b) { return b + 1 == NB ? 0 : b + 1; }
+template <int NB = kFanBins>
+__device__ __forceinline__ int prev_bin(int b) { return b == 0 ? NB - 1 : b - 1; }
+
+// a - b = s + e and a + b = s + e exactly (Knuth's two-sum, binary32
+// round to nearest; the intrinsics are never contracted into an FMA)
+__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e)
+{
+    s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Order key for the farthest-point choice of a bin: |p - c|^2 - r2ref,
+// from the differences p - c and their squares as exact pairs (two-sum,
+// two-product by FMA), rounded once at the end.  The binary32 square
+// |p - c|^2 itself resolves only 2^-23 of its value, while on the unit
+// circle the radii of binary32 points differ by about 10^-7 and the top
+// points of a bin by far less: the vertex would be any of its top points
+// and the chords sag below the others.  Any key would keep the test exact
+// (a vertex only has to be an input point); this one finds the farthest.
+// r2ref: a squared distance of the set's scale (Sterbenz: the last
+// difference is exact when the sum is within a factor 2 of it).
+__device__ __forceinline__ uint32_t far_key(float px, float py, float cx, float cy, float r2ref)
+{
+    float dxh, dxl, dyh, dyl;
+    two_diff(px, cx, dxh, dxl);
+    two_diff(py, cy, dyh, dyl);
+    const float sxh = __fmul_rn(dxh, dxh), sxl = __fmaf_rn(dxh, dxh, -sxh);
+    const float syh = __fmul_rn(dyh, dyh), syl = __fmaf_rn(dyh, dyh, -syh);
+    float sh, sl;
+    two_sum(sxh, syh, sh, sl);
+    const float cross = __fmul_rn(2.0f, __fmaf_rn(dxh, dxl, __fmul_rn(dyh, dyl)));
+    const float lo = __fadd_rn(__fadd_rn(sl, __fadd_rn(sxl, syl)), cross);
+    return ord_key(__fadd_rn(__fsub_rn(sh, r2ref), lo));
+}
+
+// r2ref of far_key for a polygon's set: the squared distance from its
+// centre to its first vertex (binary32).
+__device__ __forceinline__ float far_ref(const Octagon &o)
+{
+    const float ux = __fsub_rn(o.ax[0], o.cx), uy = __fsub_rn(o.ay[0], o.cy);
+    return __fmaf_rn(ux, ux, __fmul_rn(uy, uy));
+}
 
 // Strictly inside a fan triangle (exact signs).  V: kFanBins vertices.
 // With o = orient(c, v, p) = +1 the triangle is (c, v, w), w the next
@@ -94,33 +144,36 @@ __device__ __forceinline__ int prev_bin(int b) { return b == 0 ? kFanBins - 1 : 
 // orient(v, p, c) and orient(w, c, p) as orient(p, w, c), so that both use
 // the differences p - c of the bin; orient_f32 certifies the sign of either
 // form with the same bound.
+template <int NB = kFanBins>
 __device__ __forceinline__ int fan_signs_f32(const float2 *V, float cx, float cy, float px, float py)
 {
     const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy);
-    const int b = fan_bin(dx, dy);
+    const int b = fan_bin<NB>(dx, dy);
     const float2 v = V[b];
     const int o = orient_f32_ref(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), dx, dy);          // (v, p, c)
-    const float2 w = V[o == 1 ? next_bin(b) : prev_bin(b)];
+    const float2 w = V[o == 1 ? next_bin<NB>(b) : prev_bin<NB>(b)];
     const int e1 = orient_f32(v.x, v.y, w.x, w.y, px, py);
     const int e2 = orient_f32_ref(dx, dy, __fsub_rn(w.x, cx), __fsub_rn(w.y, cy));         // (p, w, c)
     const bool out = (e1 != 2 && e1 != o) || (e2 != 2 && e2 != o);
     return o == 2 ? 2 : (out ? 0 : (e1 == o && e2 == o ? 1 : 2));
 }
 
+template <int NB = kFanBins>
 __device__ __noinline__ bool fan_inside_exact(const float2 *V, float cx, float cy, float px, float py)
 {
-    const int b = fan_bin(px - cx, py - cy);
+    const int b = fan_bin<NB>(px - cx, py - cy);
     const float2 v = V[b];
     const int o = orient(cx, cy, v.x, v.y, px, py);
     if (o == 0) return false;
-    const float2 w = V[o > 0 ? next_bin(b) : prev_bin(b)];
+    const float2 w = V[o > 0 ? next_bin<NB>(b) : prev_bin<NB>(b)];
     return orient(v.x, v.y, w.x, w.y, px, py) == o && orient(w.x, w.y, cx, cy, px, py) == o;
 }
 
+template <int NB = kFanBins>
 __device__ __forceinline__ bool fan_inside(const float2 *V, float cx, float cy, float2 p)
 {
-    const int f = fan_signs_f32(V, cx, cy, p.x, p.y);
-    return f != 2 ? f == 1 : fan_inside_exact(V, cx, cy, p.x, p.y);
+    const int f = fan_signs_f32<NB>(V, cx, cy, p.x, p.y);
+    return f != 2 ? f == 1 : fan_inside_exact<NB>(V, cx, cy, p.x, p.y);
 }
 
 // The fan runs when the octagon left at least kKgonMinS survivors and has
@@ -157,7 +210,7 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     if (s < kKgonMinS || !oct->has_edges || oct->spec) return;
     for (int i = threadIdx.x; i < kFanBins; i += FT) s_best[i] = 0ull;
     __syncthreads();
-    const float cx = oct->cx, cy = oct->cy;
+    const float cx = oct->cx, cy = oct->cy, r2ref = far_ref(*oct);
     const int64_t ntiles = ceil_div(n, FTILE);
     const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(4, ntiles / kBinTiles));   // every stride-th tile
     const int64_t nsamp = ceil_div(ntiles, stride);
@@ -182,8 +235,8 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
             if (q < n) {
                 const float dx = p[r].x - cx, dy = p[r].y - cy;
                 const int b = fan_bin(dx, dy);
-                const float r2 = __fmaf_rn(dx, dx, dy * dy);   // >= +0
-                const unsigned long long v = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)~(uint32_t)q;
+                const unsigned long long v =
+                    ((unsigned long long)far_key(p[r].x, p[r].y, cx, cy, r2ref) << 32) | (uint32_t)~(uint32_t)q;
                 if (v > s_best[b]) atomicMax(&s_best[b], v);   // the read only saves atomics
             }
         }
@@ -571,6 +624,348 @@ cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blo
 namespace {
 
 // ---------------------------------------------------------------------------
+// second level, over the first level's survivors (the filter's scatter
+// output: sort keys and payloads in point order).  On the unit circle the
+// binary32 points scatter about 10^-7 around the circle while a chord of
+// the first fan sags 6 10^-9 below it, so a fan vertex, the farthest
+// sampled point of its bin, leaves the points near the top of that scatter
+// outside its triangles: about a sixth of the points reach the sort.  The
+// same test with kFan2Sub times as many bins, each vertex the farthest
+// survivor of its sub-bin (every survivor, not a sample), drops most of
+// those.  The vertices are again input points and the centre is the
+// first level's, so the same argument holds: a survivor strictly inside a
+// triangle (c, v, w) is no hull vertex.  Kernels (grid-wide passes, after
+// the scatter):
+//
+//  fan2_max_kernel      whether the level runs (the first level's centre
+//                       was proven inside and at least kFan2MinS points,
+//                       or the tuned minimum, survived); per sub-bin the
+//                       farthest survivor
+//  fan2_build_kernel    the vertex of every sub-bin (the previous
+//                       non-empty one for an empty sub-bin, cyclically)
+//  fan2_test_kernel     per tile of 4096 survivors the exact test, keep bits
+//                       and counts (in the filter's keep-bit, tile-count and
+//                       block-total buffers, free by then)
+//  fan2_scatter_kernel  the kept survivors, in their order, into the sort's
+//                       second buffers; the sort then reads those
+// ---------------------------------------------------------------------------
+constexpr int F2T = 256;
+static_assert(kFan2Bins % BT == 0, "sub-bins split evenly over the build blocks");
+static_assert(F2T == kFiltThreads, "the test pass keeps the filter's keep-bit layout");
+
+__device__ __forceinline__ float2 surv_point(const uint32_t *keys, const unsigned long long *pay, uint32_t i)
+{
+    return make_float2(key_float(keys[i]), key_float((uint32_t)(pay[i] >> 32)));
+}
+
+__global__ void __launch_bounds__(F2T) fan2_max_kernel(void *ws, Layout L, uint32_t min_s)
+{
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const Kgon *g = at<Kgon>(ws, L.kgon);
+    const uint32_t m = at<Ctrl>(ws, L.ctrl)->surv_count;
+    // g->ok is this call's: the fan kernels ran before (they clear it when
+    // the fan does not run)
+    const bool on = !oct->abort && g->ok && m >= min_s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Fan2Ctrl *f2 = at<Fan2Ctrl>(ws, L.fan2);
+        f2->on = on ? 1u : 0u;
+        f2->count_in = on ? m : 0u;
+    }
+    if (!on) return;
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
+    unsigned long long *slot = at<unsigned long long>(ws, L.fan2_slot);
+    const float cx = g->cx, cy = g->cy, r2ref = far_ref(*oct);
+    for (uint32_t i = blockIdx.x * F2T + threadIdx.x; i < m; i += gridDim.x * F2T) {
+        const float2 p = surv_point(keys, pay, i);
+        const float dx = __fsub_rn(p.x, cx), dy = __fsub_rn(p.y, cy);
+        const int b = fan_bin<kFan2Bins>(dx, dy);
+        const unsigned long long v = ((unsigned long long)far_key(p.x, p.y, cx, cy, r2ref) << 32) | (uint32_t)~i;
+        if (v > __ldcg(&slot[b])) atomicMax(&slot[b], v);   // the read only saves atomics
+    }
+}
+
+// One thread per sub-bin, as fan_build_kernel.
+__global__ void __launch_bounds__(BT) fan2_build_kernel(void *ws, Layout L)
+{
+    __shared__ int s_w[BT / 32];
+    __shared__ int s_scan[BT / 32];
+    Fan2Ctrl *f2 = at<Fan2Ctrl>(ws, L.fan2);
+    if (!f2->on) return;
+    const unsigned long long *slot = at<unsigned long long>(ws, L.fan2_slot);
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
+    float2 *V = at<float2>(ws, L.fan2_v);
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const int b = (int)(blockIdx.x * BT + tid);
+    const unsigned long long mine = slot[b];
+    int incl = mine != 0ull ? b : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl = max(incl, u);
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    for (int w = 0; w < (int)warp; ++w) incl = max(incl, s_scan[w]);
+    int prev = -1;
+    for (uint32_t k = 1; k <= gridDim.x && prev < 0; ++k) {   // prev is block-uniform
+        const uint32_t rb = (blockIdx.x + gridDim.x - k) % gridDim.x;
+        const int j = (int)(rb * BT + tid);
+        prev = block_max(slot[j] != 0ull ? j : -1, s_w);
+    }
+    if (prev < 0) {   // no survivor reached a slot: keep everything
+        if (tid == 0) f2->bad = 1u;
+        return;
+    }
+    const int cur = incl >= 0 ? incl : prev;
+    const uint32_t i = ~(uint32_t)(cur == b ? mine : slot[cur]);
+    V[b] = surv_point(keys, pay, i);
+}
+
+// Per-tile survivor counts of a window of tiles, added up in shared memory
+// as the warps finish each tile (as in the filter's count pass).
+constexpr int kF2Ring = 256;
+
+__global__ void __launch_bounds__(F2T) fan2_test_kernel(void *ws, Layout L)
+{
+    __shared__ uint32_t s_cnt[kF2Ring];
+    __shared__ uint32_t s_w[F2T / 32];
+    const Fan2Ctrl *f2 = at<Fan2Ctrl>(ws, L.fan2);
+    if (!f2->on) return;
+    const uint32_t m = f2->count_in;
+    const bool none = f2->bad != 0u;
+    const Kgon *g = at<Kgon>(ws, L.kgon);
+    const float cx = g->cx, cy = g->cy;
+    const float2 *V = at<float2>(ws, L.fan2_v);
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
+    uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    for (int i = threadIdx.x; i < kF2Ring; i += F2T) s_cnt[i] = 0u;
+    __syncthreads();
+    const int64_t ntiles = ceil_div((int64_t)m, kFiltTile);
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t t1 = std::min<int64_t>(ntiles, (int64_t)(blockIdx.x + 1) * per);
+    uint32_t part = 0;
+    for (int64_t w0 = (int64_t)blockIdx.x * per; w0 < t1; w0 += kF2Ring) {
+        const int64_t w1 = std::min<int64_t>(t1, w0 + kF2Ring);
+        for (int64_t tile = w0; tile < w1; ++tile) {
+            const uint32_t base = (uint32_t)(tile * kFiltTile);
+            uint32_t keep = 0;
+#pragma unroll 4
+            for (int r = 0; r < kFiltItems; ++r) {
+                const uint32_t i = base + r * F2T + threadIdx.x;
+                if (i < m && (none || !fan_inside<kFan2Bins>(V, cx, cy, surv_point(keys, pay, i)))) keep |= 1u << r;
+            }
+            bits[tile * F2T + threadIdx.x] = (uint16_t)keep;
+            uint32_t c = __popc(keep);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane_id() == 0 && c) atomicAdd(&s_cnt[tile - w0], c);
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < w1 - w0; i += F2T) {
+            const uint32_t v = s_cnt[i];
+            status[w0 + i] = v;
+            s_cnt[i] = 0u;
+            part += v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane_id() == 0) s_w[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < F2T / 32; ++w) t += s_w[w];
+        at<uint32_t>(ws, L.filt_bsum)[blockIdx.x] = t;
+    }
+}
+
+// One warp writes the kept survivors of one tile in order (thread t of the
+// test pass held items base + r * 256 + t, r < 16: eight groups of 32
+// threads, each row's first output position from the warp's row counts).
+__device__ __forceinline__ void fan2_scatter_tile(const uint32_t *__restrict__ keys,
+                                                  const unsigned long long *__restrict__ pay,
+                                                  const uint16_t *__restrict__ tbits, uint32_t base, uint32_t out_off,
+                                                  uint32_t *out_keys, unsigned long long *out_pay)
+{
+    const uint32_t lane = lane_id(), lt = (1u << lane) - 1u;
+    uint32_t kb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) kb[k] = tbits[k * 32 + lane];
+    uint32_t racc[kFiltItems];
+    {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = kb[2 * j] | (kb[2 * j + 1] << 16);
+        uint32_t run = out_off;
+#pragma unroll
+        for (int r = 0; r < kFiltItems; ++r) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c += __popc(w[j] & (0x10001u << r));
+            racc[r] = run;
+            run += __reduce_add_sync(0xffffffffu, c);
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t kbk = tbits[k * 32 + lane];
+        if (!__any_sync(0xffffffffu, kbk != 0u)) continue;
+        const uint32_t t = k * 32 + lane;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t kv[8];
+            unsigned long long pv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = 8 * h + q;
+                kv[q] = 0u;
+                pv[q] = 0ull;
+                if ((kbk >> r) & 1u) {
+                    kv[q] = keys[base + r * F2T + t];
+                    pv[q] = pay[base + r * F2T + t];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int r = 8 * h + q;
+                const uint32_t mk = (kbk >> r) & 1u;
+                const uint32_t b0 = __ballot_sync(0xffffffffu, mk);
+                if (!b0) continue;
+                const uint32_t pos = racc[r] + __popc(b0 & lt);
+                racc[r] += __popc(b0);
+                if (mk) {
+                    out_keys[pos] = kv[q];
+                    out_pay[pos] = pv[q];
+                }
+            }
+        }
+    }
+}
+
+// Launched with the test pass's grid: block b owns the same tile range, its
+// output offset the earlier blocks' totals.  Block 0 hands the kept list to
+// the sort (count, buffer 1).
+__global__ void __launch_bounds__(F2T) fan2_scatter_kernel(void *ws, Layout L)
+{
+    __shared__ uint32_t s_red[2][F2T / 32];
+    __shared__ uint32_t s_list[F2T];
+    __shared__ uint32_t s_loff[F2T];
+    __shared__ uint32_t s_nlist;
+    const Fan2Ctrl *f2 = at<Fan2Ctrl>(ws, L.fan2);
+    if (!f2->on) return;
+    const uint32_t m = f2->count_in;
+    const unsigned long long *status = at<unsigned long long>(ws, L.filt_status);
+    const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
+    const uint16_t *bits = at<uint16_t>(ws, L.keep_bits);
+    const uint32_t *keys = at<uint32_t>(ws, L.keys[0]);
+    const unsigned long long *pay = at<unsigned long long>(ws, L.pay[0]);
+    uint32_t *out_keys = at<uint32_t>(ws, L.keys[1]);
+    unsigned long long *out_pay = at<unsigned long long>(ws, L.pay[1]);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    constexpr int NWF = F2T / 32;
+    uint32_t before = 0, total = 0;
+    for (uint32_t i = tid; i < gridDim.x; i += F2T) {
+        const uint32_t v = bsum[i];
+        total += v;
+        if (i < blockIdx.x) before += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = before;
+        s_red[1][warp] = total;
+    }
+    __syncthreads();
+    before = total = 0;
+#pragma unroll
+    for (int w = 0; w < NWF; ++w) {
+        before += s_red[0][w];
+        total += s_red[1][w];
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+        ctrl->surv_count = total;
+        ctrl->sort_in = 1u;
+    }
+    __syncthreads();   // s_red is reused below
+    const int64_t ntiles = ceil_div((int64_t)m, kFiltTile);
+    const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = std::min<int64_t>(ntiles, r0 + per);
+    uint32_t run = before;
+    for (int64_t c0 = r0; c0 < r1; c0 += F2T) {
+        const int64_t t = c0 + tid;
+        const uint32_t cnt = t < r1 ? (uint32_t)(status[t] & 0xffffffffull) : 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += u;
+        }
+        const uint32_t nz = __ballot_sync(0xffffffffu, cnt != 0u);
+        if (lane == 31) {
+            s_red[0][warp] = incl;
+            s_red[1][warp] = __popc(nz);
+        }
+        __syncthreads();
+        uint32_t wbefore = 0, chunk_total = 0, lbefore = 0, nlist = 0;
+#pragma unroll
+        for (int w = 0; w < NWF; ++w) {
+            if (w < (int)warp) {
+                wbefore += s_red[0][w];
+                lbefore += s_red[1][w];
+            }
+            chunk_total += s_red[0][w];
+            nlist += s_red[1][w];
+        }
+        if (cnt != 0u) {
+            const uint32_t slot = lbefore + __popc(nz & ((1u << lane) - 1u));
+            s_list[slot] = tid;
+            s_loff[slot] = run + wbefore + incl - cnt;
+        }
+        if (tid == 0) s_nlist = nlist;
+        __syncthreads();
+        const uint32_t nl = s_nlist;
+        for (uint32_t li = warp; li < nl; li += NWF) {
+            const int64_t tile = c0 + s_list[li];
+            fan2_scatter_tile(keys, pay, bits + tile * F2T, (uint32_t)(tile * kFiltTile), s_loff[li], out_keys,
+                              out_pay);
+        }
+        __syncthreads();   // s_list, s_loff and s_red are rebuilt for the next chunk
+        run += chunk_total;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fan2(int64_t n, void *ws, const Layout &L, cudaStream_t st)
+{
+    if (L.fan2_bins == 0) return cudaSuccess;   // a set too small for the second level
+    const int sms = sm_count();
+    const int64_t tiles = ceil_div(n, kFiltTile);   // survivor tiles at most
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((int64_t)sms * 4, kFiltMaxBlocks), tiles));
+    probe_before(CH_K_KGON, st);
+    const int lg = tune_value(CH_TUNE_FAN2_MIN_LOG2);
+    const uint32_t min_s = lg ? (uint32_t)(1ull << lg) : kFan2MinS;
+    fan2_max_kernel<<<sms * 8, F2T, 0, st>>>(ws, L, min_s);
+    fan2_build_kernel<<<kFan2Bins / BT, BT, 0, st>>>(ws, L);
+    fan2_test_kernel<<<(unsigned)grid, F2T, 0, st>>>(ws, L);
+    fan2_scatter_kernel<<<(unsigned)grid, F2T, 0, st>>>(ws, L);
+    note_kernels(CH_K_KGON, 4);
+    probe_after(CH_K_KGON, st);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
 // many sets (ch_hull_batched): the same fan for every set with at least
 // kKgonMinS octagon survivors, between the batched count pass and its scan
 // ---------------------------------------------------------------------------
@@ -644,7 +1039,7 @@ __global__ void __launch_bounds__(1024) bx_fan_select_kernel(void *ws, Layout L,
 }
 
 // Per work item, every kBxBinStride-th tile (counted from the set's first):
-// each point's bin around the set's box centre, packed (r^2 bits << 32 |
+// each point's bin around the set's box centre, packed (far_key << 32 |
 // ~index) into the fan's global slots by atomicMax (the read first saves
 // most atomics).
 __global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict__ pts, void *ws, Layout L,
@@ -661,7 +1056,7 @@ __global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict
         const uint2 item = items[w];
         const uint32_t b = fan_set[item.x];
         const SetInfo &S = sets[b];
-        const float cx = octs[b].cx, cy = octs[b].cy;
+        const float cx = octs[b].cx, cy = octs[b].cy, r2ref = far_ref(octs[b]);
         const float2 *p2 = reinterpret_cast<const float2 *>(pts) + S.pt_begin;
         unsigned long long *sl = slots + (size_t)item.x * kFanBins;
         const uint32_t tend = min(item.y + chunk, S.tile_base + S.ntiles);
@@ -680,8 +1075,8 @@ __global__ void __launch_bounds__(FT) bx_fan_bins_kernel(const float *__restrict
                 if (i < hi) {
                     const float dx = p[r].x - cx, dy = p[r].y - cy;
                     const int bin = fan_bin(dx, dy);
-                    const float r2 = __fmaf_rn(dx, dx, dy * dy);
-                    const unsigned long long v = ((unsigned long long)__float_as_uint(r2) << 32) | (uint32_t)~(uint32_t)i;
+                    const unsigned long long v =
+                        ((unsigned long long)far_key(p[r].x, p[r].y, cx, cy, r2ref) << 32) | (uint32_t)~(uint32_t)i;
                     if (v > __ldcg(sl + bin)) atomicMax(sl + bin, v);
                 }
             }

@@ -84,6 +84,11 @@ cudaError_t launch_learned_choice(const float *pts, int64_t n, const void *param
 // hull step: the fan test applied to the keep bits, tile counts and block
 // totals that the filter's count pass (filter_blocks blocks) left in ws;
 // may do nothing.  vec: the count pass used 16-byte point pairs.
+// The second fan level over the survivors the filter's scatter wrote (sort
+// keys and payloads in buffer 0): when it runs, the kept ones go to buffer 1
+// and the sort reads those (Ctrl::sort_in).  After launch_fan and the
+// scatter of the same call; does nothing for sets without its tables.
+cudaError_t launch_fan2(int64_t n, void *ws, const Layout &L, cudaStream_t st);
 cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blocks, void *ws, const Layout &L,
                        cudaStream_t st);
 

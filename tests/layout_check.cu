@@ -41,6 +41,8 @@ static void check_single(int64_t n, int64_t sets)
         {"ctrl", L.ctrl, sizeof(Ctrl)},
         {"filt_status", L.filt_status, ft * 8},
         {"kgon_ctrl", L.kgon_ctrl, sizeof(KgonCtrl)},
+        {"fan2", L.fan2, sizeof(Fan2Ctrl)},
+        {"fan2_slot", L.fan2_slot, (size_t)L.fan2_bins * 8},
         {"node_cnt", L.node_cnt, (size_t)L.n_nodes * 4},
         {"emit_status0", L.emit_status[0], (size_t)L.emit_tiles * 8},
         {"emit_status1", L.emit_status[1], (size_t)L.emit_tiles * 8},
@@ -63,6 +65,7 @@ static void check_single(int64_t n, int64_t sets)
         {"spec", L.spec, sizeof(SpecCtrl)},
         {"p0", L.p0, 256},
         {"learn", L.learn, sizeof(LearnScratch)},
+        {"fan2_v", L.fan2_v, (size_t)L.fan2_bins * 8},
     };
     for (size_t i = 0; i < r.size(); ++i) {
         CHECK(r[i].at % 256 == 0, "n=%lld sets=%lld: %s not 256-aligned", (long long)n, (long long)sets, r[i].name);
@@ -72,7 +75,8 @@ static void check_single(int64_t n, int64_t sets)
     }
     // the zeroed range: ctrl .. end of emit_status[1]
     const size_t z0 = L.ctrl, z1 = L.ctrl + L.zero_words * 8;
-    for (const char *need : {"ctrl", "filt_status", "kgon_ctrl", "node_cnt", "emit_status0", "emit_status1"})
+    for (const char *need : {"ctrl", "filt_status", "kgon_ctrl", "fan2", "fan2_slot", "node_cnt", "emit_status0",
+                             "emit_status1"})
         for (const Region &x : r)
             if (std::string(x.name) == need)
                 CHECK(x.at >= z0 && x.at + x.bytes <= z1, "n=%lld: %s outside the zeroed range", (long long)n, need);
@@ -82,6 +86,11 @@ static void check_single(int64_t n, int64_t sets)
                 CHECK(x.at + x.bytes <= z0 || x.at >= z1, "n=%lld: %s inside the zeroed range", (long long)n, keep);
     // the fan's per-tile scratch fits the filter's
     CHECK(ft * kFiltThreads * 2 >= ft * 512, "keep bits per tile");
+    // the second fan level: tables for large single sets only; its keep
+    // bits, tile counts and block totals reuse the filter's (one survivor
+    // tile per point tile at most)
+    CHECK(L.fan2_bins == ((sets == 0 && n >= kFan2MinN) ? kFan2Bins : 0), "n=%lld sets=%lld: fan2 tables",
+          (long long)n, (long long)sets);
     if (sets > 0) {
         const BatchLayout B = make_batch_layout(L, sets);
         CHECK(B.sets >= L.total && B.sets % 256 == 0, "sets=%lld: batch records overlap", (long long)sets);

@@ -27,6 +27,17 @@ def test_algorithmic_bytes_definitions():
     assert bench.algorithmic_bytes("emit", N, S, T) is None
 
 
+def test_algorithmic_bytes_with_the_second_fan_level():
+    # the circle set's first level left F[1] points, its second level T[1]:
+    # the filter wrote F, the fan group read the octagon survivors, then the
+    # first level's survivors twice, and copied the second level's
+    F = [69, 16_543_492, 118_191]
+    T2 = [69, 600_000, 118_191]
+    assert bench.algorithmic_bytes("filter", N, S, T2, F) == sum(8 * N + 12 * f for f in F)
+    assert bench.algorithmic_bytes("kgon", N, S, T2, F) == (8 * S[1] + 24 * F[1] + 24 * T2[1]) + 8 * S[2]
+    assert bench.algorithmic_bytes("sort_pass", N, S, T2, F) == sum(4 * 24 * t for t in T2[1:])
+
+
 @pytest.fixture
 def one_device(monkeypatch):
     class Props:

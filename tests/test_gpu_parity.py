@@ -268,7 +268,7 @@ def test_fan_removes_points_and_keeps_the_hull(dist, aligned):
     hidx, hcnt = ch.convex_hull(d, ws)
     torch.cuda.synchronize()
     assert ch.ch_last_error(ws.buf) == ch.CH_OK
-    s_oct, t, _ = ch.ch_hull_counts(ws.buf, len(p))
+    s_oct, t, _, _ = ch.ch_hull_counts(ws.buf, len(p))
     _, os_, oh = oracle.convex_hull(p)
     assert s_oct == len(os_)
     assert t < (s_oct if dist == "circle" else s_oct // 4), (s_oct, t)

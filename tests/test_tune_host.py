@@ -13,12 +13,14 @@ def test_knobs_round_trip_and_reject_bad_values():
     try:
         for k in ch.TUNE_KNOBS:
             assert ch.ch_tune_get(k) == 0
-            v = {"bx_fan_chunk": 16, "bx_ext_items": 8}.get(k, 5)
+            v = {"bx_fan_chunk": 16, "bx_ext_items": 8, "fan2_min_log2": 12}.get(k, 5)
             ch.ch_tune_set(k, v)
             assert ch.ch_tune_get(k) == v
         assert lib.ch_tune_set(len(ch.TUNE_KNOBS), 1) == ch.CH_ERR_ARG
         assert lib.ch_tune_set(ch.TUNE_KNOBS.index("bx_fan_chunk"), 12) == ch.CH_ERR_ARG
         assert lib.ch_tune_set(ch.TUNE_KNOBS.index("bx_ext_items"), 5) == ch.CH_ERR_ARG
+        assert lib.ch_tune_set(ch.TUNE_KNOBS.index("fan2_min_log2"), 9) == ch.CH_ERR_ARG
+        assert lib.ch_tune_set(ch.TUNE_KNOBS.index("fan2_min_log2"), 32) == ch.CH_ERR_ARG
         assert lib.ch_tune_set(-1, 1) == ch.CH_ERR_ARG
         assert lib.ch_tune_set(0, 65) == ch.CH_ERR_ARG
         assert lib.ch_tune_set(0, -1) == ch.CH_ERR_ARG
