@@ -818,11 +818,14 @@ __global__ void __launch_bounds__(32) bx_merge_kernel(void *ws, Layout L, BatchL
 // search over the tile's offsets.  Side 0 goes to out0, side 1 to out1.
 // With sc_off, each super-chunk's output offset per side is recorded too
 // (sc_off[side][nc] = side total).
+// copy = false: only the offsets (sc_off required); emit_copy_kernel then
+// writes the ranges with the whole grid.
 struct EmitArgs {
     uint32_t *out[2];
     uint32_t *sc_off[2];
     uint32_t *ticket;
     uint32_t *h_total[2];
+    bool copy;
 };
 
 __device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t nc, uint64_t s, const EmitArgs &E)
@@ -903,6 +906,7 @@ __device__ void emit_body(void *ws, const Layout &L, const ChainPtrs &P, int64_t
             if (E.sc_off[side] && c < nc) E.sc_off[side][c] = (uint32_t)(s_excl[side] + rel);
         }
         __syncthreads();
+        if (!E.copy) continue;   // (the loop's first barrier orders the next tile's shared writes)
         constexpr int B4 = 4;   // output positions per thread in flight
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -947,9 +951,47 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(void *ws, Layout L, 
     const uint32_t s = hull_stage_count(ctrl, oct);
     if (s == 0) return;
     const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
-    EmitArgs E{{hull_idx, at<uint32_t>(ws, L.utmp)}, {nullptr, nullptr}, &ctrl->emit_ticket[0],
-               {&ctrl->h_lower, &ctrl->h_upper}};
+    EmitArgs E{{hull_idx, at<uint32_t>(ws, L.utmp)},
+               {at<uint32_t>(ws, L.emit_off[0]), at<uint32_t>(ws, L.emit_off[1])},
+               &ctrl->emit_ticket[0],
+               {&ctrl->h_lower, &ctrl->h_upper},
+               false};
     emit_body(ws, L, P, ceil_div((int64_t)s, SC), s, E);
+}
+
+// The chains' surviving ranges into the outputs (lower chain to hull_idx,
+// upper chain to utmp: original indices, the low half of the payload),
+// every thread of the grid on its own output positions: the super-chunk
+// of position k is the last one whose offset (emit_off) is at most k
+// (binary search; an empty range shares its offset with the next one).
+// A hull with many vertices on few super-chunks (the unit circle after
+// the fan: about 2000 per super-chunk) is no longer copied by one block.
+__global__ void __launch_bounds__(kEmitThreads) emit_copy_kernel(void *ws, Layout L, uint32_t *hull_idx)
+{
+    const Ctrl *ctrl = at<Ctrl>(ws, L.ctrl);
+    const Octagon *oct = at<Octagon>(ws, L.oct);
+    const uint32_t s = hull_stage_count(ctrl, oct);
+    if (s == 0) return;
+    const ChainPtrs P = chain_ptrs(ws, L, ctrl->final_buf);
+    const int32_t nc = (int32_t)ceil_div((int64_t)s, SC);
+    const uint32_t gtid = blockIdx.x * kEmitThreads + threadIdx.x, gthreads = gridDim.x * kEmitThreads;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const uint32_t T = side ? ctrl->h_upper : ctrl->h_lower;
+        const uint32_t *off = at<uint32_t>(ws, L.emit_off[side]);
+        uint32_t *out = side ? at<uint32_t>(ws, L.utmp) : hull_idx;
+        for (uint32_t k = gtid; k < T && k < s; k += gthreads) {
+            int lo_j = 0, hi_j = nc - 1;
+            while (lo_j < hi_j) {
+                const int mid = (lo_j + hi_j + 1) >> 1;
+                if (__ldg(off + mid) <= k) lo_j = mid;
+                else hi_j = mid - 1;
+            }
+            const uint32_t sp =
+                __ldcg(P.pos[side] + (int64_t)lo_j * CS + __ldcg(P.lo[side] + lo_j) + (k - __ldg(off + lo_j)));
+            out[k] = (uint32_t)__ldg(P.pay + sp);
+        }
+    }
 }
 
 // all sets at once: lower chains to the batch's lower array, upper chains
@@ -964,7 +1006,8 @@ __global__ void __launch_bounds__(kEmitThreads) bx_emit_kernel(void *ws, Layout 
     EmitArgs E{{at<uint32_t>(ws, BL.lower), at<uint32_t>(ws, L.utmp)},
                {at<uint32_t>(ws, BL.sc_off[0]), at<uint32_t>(ws, BL.sc_off[1])},
                &bc->emit_ticket,
-               {&bc->h_lower, &bc->h_upper}};
+               {&bc->h_lower, &bc->h_upper},
+               true};
     emit_body(ws, L, P, nc, (uint64_t)L.n, E);
 }
 
@@ -1106,7 +1149,8 @@ cudaError_t launch_chain(void *ws, const Layout &L, uint32_t *hull_idx, uint32_t
     if (eb < 1) eb = 1;
     probe_before(CH_K_EMIT, st);
     emit_kernel<<<(unsigned)eb, kEmitThreads, 0, st>>>(ws, L, hull_idx);
-    note_kernels(CH_K_EMIT, 1);
+    emit_copy_kernel<<<(unsigned)sms * 4, kEmitThreads, 0, st>>>(ws, L, hull_idx);
+    note_kernels(CH_K_EMIT, 2);
     probe_after(CH_K_EMIT, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -221,6 +221,7 @@ struct Layout {
     size_t chain_pt[2];     // float2[n_chunks * kChainStride]: their coordinates
     size_t chunk;           // int32[8 * n_chunks]: loL hiL loU hiU prvL nxtL prvU nxtU
     size_t node;            // int32[4 * n_nodes]: firstL lastL firstU lastU
+    size_t emit_off[2];     // u32[n_chunks + 1]: output offset of each super-chunk's chain range, per side
     size_t keep_bits;       // u16[filt_tiles * kFiltThreads]: keep decisions of the count pass
     size_t filt_bsum;       // u32[kFiltMaxBlocks]: survivors per block of the count pass
     size_t kgon;            // Kgon
@@ -357,6 +358,8 @@ __host__ __device__ inline Layout make_layout(int64_t n, int64_t sets = 0)
     }
     L.chunk = take((size_t)L.n_chunks * 8 * 4);
     L.node = take((size_t)L.n_nodes * 4 * 4);
+    L.emit_off[0] = take((size_t)(L.n_chunks + 1) * 4);
+    L.emit_off[1] = take((size_t)(L.n_chunks + 1) * 4);
     L.keep_bits = take((size_t)L.filt_tiles * kFiltThreads * 2);
     L.filt_bsum = take((size_t)kFiltMaxBlocks * 4);
     L.kgon = take(sizeof(Kgon));

@@ -58,6 +58,8 @@ static void check_single(int64_t n, int64_t sets)
         {"chain_pt1", L.chain_pt[1], nc * kChainStride * 8},
         {"chunk", L.chunk, nc * 8 * 4},
         {"node", L.node, (size_t)L.n_nodes * 4 * 4},
+        {"emit_off0", L.emit_off[0], (nc + 1) * 4},
+        {"emit_off1", L.emit_off[1], (nc + 1) * 4},
         {"keep_bits", L.keep_bits, ft * kFiltThreads * 2},
         {"filt_bsum", L.filt_bsum, (size_t)kFiltMaxBlocks * 4},
         {"kgon", L.kgon, sizeof(Kgon)},
