@@ -753,10 +753,33 @@ __global__ void __launch_bounds__(F2T) fan2_test_kernel(void *ws, Layout L)
         for (int64_t tile = w0; tile < w1; ++tile) {
             const uint32_t base = (uint32_t)(tile * kFiltTile);
             uint32_t keep = 0;
-#pragma unroll 4
-            for (int r = 0; r < kFiltItems; ++r) {
-                const uint32_t i = base + r * F2T + threadIdx.x;
-                if (i < m && (none || !fan_inside<kFan2Bins>(V, cx, cy, surv_point(keys, pay, i)))) keep |= 1u << r;
+            // eight survivors at a time: binary32 signs without branches (the
+            // table loads of the eight overlap), then the exact tiers for
+            // the undecided ones
+#pragma unroll 1
+            for (int h = 0; h < kFiltItems / 8; ++h) {
+                float2 q[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t i = base + (8 * h + k) * F2T + threadIdx.x;
+                    q[k] = i < m ? surv_point(keys, pay, i) : make_float2(cx, cy);
+                }
+                uint32_t live = 0, in = 0, und = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    live |= (base + (8 * h + k) * F2T + threadIdx.x < m ? 1u : 0u) << k;
+                    const int f = fan_signs_f32<kFan2Bins>(V, cx, cy, q[k].x, q[k].y);
+                    in |= (f == 1 ? 1u : 0u) << k;
+                    und |= (f == 2 ? 1u : 0u) << k;
+                }
+                und &= live;   // (positions past the list hold the centre: never read again)
+                while (und) {
+                    const int k = __ffs(und) - 1;
+                    und &= und - 1u;
+                    const float2 p = surv_point(keys, pay, base + (8 * h + k) * F2T + threadIdx.x);
+                    if (fan_inside_exact<kFan2Bins>(V, cx, cy, p.x, p.y)) in |= 1u << k;
+                }
+                keep |= (live & (none ? 0xffu : ~in)) << (8 * h);
             }
             bits[tile * F2T + threadIdx.x] = (uint16_t)keep;
             uint32_t c = __popc(keep);
