@@ -49,7 +49,7 @@ constexpr int FITEMS = 8;                // points per thread per tile there
 constexpr int FTILE = FT * FITEMS;       // 4096
 constexpr int CT = 1024;                 // threads per block of the refine pass: four
 constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, each with its own tiles
-constexpr int64_t kBinTiles = 1536;      // the bins see every min(4, tiles / kBinTiles)-th tile (at least every tile)
+constexpr int64_t kBinTiles = 1536;      // the bins see every min(8, tiles / kBinTiles)-th tile (at least every tile)
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
 static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
@@ -72,8 +72,10 @@ __device__ __forceinline__ int fan_bin(float dx, float dy)
         const float t = __fdividef(dy, s);
         a = dx >= 0.0f ? (dy >= 0.0f ? t : 4.0f + t) : 2.0f - t;
     }
+    // a is in [0, 4] (t in [-1, 1]; a NaN from an overflowed difference
+    // converts to 0): only the top needs a clamp
     const int b = __float2int_rz(a * (NB / 4.0f));
-    return b < 0 ? 0 : (b >= NB ? NB - 1 : b);
+    return min(b, NB - 1);
 }
 
 template <int NB = kFanBins>
@@ -144,18 +146,39 @@ __device__ __forceinline__ float far_ref(const Octagon &o)
 // orient(v, p, c) and orient(w, c, p) as orient(p, w, c), so that both use
 // the differences p - c of the bin; orient_f32 certifies the sign of either
 // form with the same bound.
+// The signs orient_f32 certifies, as two flags (det > bound, -det > bound;
+// neither when undecided or when the terms may have overflowed): the same
+// arithmetic on the rounded differences a - c and b - c, without turning
+// the flags into an integer.
+struct Sgn {
+    bool pos, neg;
+};
+__device__ __forceinline__ Sgn sgn_ref(float acx, float acy, float bcx, float bcy)
+{
+    const float detleft = __fmul_rn(acx, bcy);
+    const float detright = __fmul_rn(acy, bcx);
+    const float det = __fsub_rn(detleft, detright);
+    const float detsum = __fadd_rn(fabsf(detleft), fabsf(detright));
+    const float eb = __fmaf_ru(detsum, 2.384185791015625e-07f /* 2^-22 */, 7.174648137343064e-43f /* 2^-140 */);
+    const bool ok = detsum <= 3.0e38f;
+    return {ok && det > eb, ok && -det > eb};
+}
+
 template <int NB = kFanBins>
 __device__ __forceinline__ int fan_signs_f32(const float2 *V, float cx, float cy, float px, float py)
 {
     const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy);
     const int b = fan_bin<NB>(dx, dy);
     const float2 v = V[b];
-    const int o = orient_f32_ref(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), dx, dy);          // (v, p, c)
-    const float2 w = V[o == 1 ? next_bin<NB>(b) : prev_bin<NB>(b)];
-    const int e1 = orient_f32(v.x, v.y, w.x, w.y, px, py);
-    const int e2 = orient_f32_ref(dx, dy, __fsub_rn(w.x, cx), __fsub_rn(w.y, cy));         // (p, w, c)
-    const bool out = (e1 != 2 && e1 != o) || (e2 != 2 && e2 != o);
-    return o == 2 ? 2 : (out ? 0 : (e1 == o && e2 == o ? 1 : 2));
+    const Sgn o = sgn_ref(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), dx, dy);                   // (v, p, c)
+    const float2 w = V[o.pos ? next_bin<NB>(b) : prev_bin<NB>(b)];
+    const Sgn e1 = sgn_ref(__fsub_rn(v.x, px), __fsub_rn(v.y, py), __fsub_rn(w.x, px), __fsub_rn(w.y, py));   // (v, w, p)
+    const Sgn e2 = sgn_ref(dx, dy, __fsub_rn(w.x, cx), __fsub_rn(w.y, cy));                   // (p, w, c)
+    // inside: the three signs certified equal (strictly inside the triangle
+    // on o's side); outside: one of the edges certified opposite to o
+    const bool in = (o.pos && e1.pos && e2.pos) || (o.neg && e1.neg && e2.neg);
+    const bool out = (o.pos && (e1.neg || e2.neg)) || (o.neg && (e1.pos || e2.pos));
+    return in ? 1 : (out ? 0 : 2);
 }
 
 template <int NB = kFanBins>
@@ -212,7 +235,7 @@ __global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ 
     __syncthreads();
     const float cx = oct->cx, cy = oct->cy, r2ref = far_ref(*oct);
     const int64_t ntiles = ceil_div(n, FTILE);
-    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(4, ntiles / kBinTiles));   // every stride-th tile
+    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(8, ntiles / kBinTiles));   // every stride-th tile
     const int64_t nsamp = ceil_div(ntiles, stride);
     // two sample tiles per trip (k and k + grid: twice the loads in flight
     // of one 512-thread block per SM); the next two stream into L2 meanwhile
