@@ -113,11 +113,16 @@ __device__ __forceinline__ void pack_edges(OctSmem &so, const Octagon &o)
 // keep (outside the vertices' box, or proven not strictly left of the edge
 // facing it), 2 deferred (likely strictly inside: every edge must be
 // tested).  The facing edge is the one of p's octant around the box centre,
-// picked without branches; any edge would give the same final decisions
-// (a 1 is a proof, a 2 is tested in full).
+// picked without branches (on a circle the lanes of a warp face every
+// octant); any edge would give the same final decisions (a 1 is a proof, a
+// 2 is tested in full).
 template <bool BOX>
 __device__ __forceinline__ uint32_t first_look(const OctSmem &o, float x, float y)
 {
+    // the rectangle first, as an early exit: it holds nearly every point of
+    // a normal cloud (whole warps skip the rest) and none of a circle's
+    if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) return 0u;
+    if (!o.has_edges || outside_box<BOX>(o, x, y)) return 1u;
     const float ux = x - o.cx, uy = y - o.cy;
     const float aux = fabsf(ux), auy = fabsf(uy);
     const uint32_t q = uy < 0.0f ? (ux < 0.0f ? 2u : 3u) : (ux < 0.0f ? 1u : 0u);   // quadrant
@@ -126,10 +131,7 @@ __device__ __forceinline__ uint32_t first_look(const OctSmem &o, float x, float 
     const float u = __fsub_rn(x, d.x);
     const float v = __fsub_rn(y, d.y);
     const float t = __fsub_rn(__fmul_rn(d.z, v), __fmul_rn(d.w, u));
-    uint32_t c = t < -o.eb[e] ? 1u : 2u;
-    if (!o.has_edges || outside_box<BOX>(o, x, y)) c = 1u;
-    if (x >= o.xl && x <= o.xh && y >= o.yl && y <= o.yh) c = 0u;
-    return c;
+    return t < -o.eb[e] ? 1u : 2u;
 }
 
 // Deferred points, spread over the lanes, would hold whole warps in the
@@ -653,9 +655,15 @@ __device__ void spec_scatter(SpecScatterSmem &sm, void *ws, const Layout &L, uin
 // scan turns it into (offset << 32 | count).  Each thread's 16 keep bits go
 // to keep_bits, so the scatter pass does not test again.
 // Per-tile survivor counts of a window of kCountRing tiles, added up in
-// shared memory by the warps as they finish each tile (no barrier per
-// tile: the warps of a block drift apart and their loads overlap), written
-// to filt_status when the window is done.
+// shared memory by the warps as they finish each tile, written to
+// filt_status when the window is done.  Schedule, chosen by each block
+// from its first tile: where it keeps under a quarter of its points (the
+// rectangle settles most of them: bound by memory) the warps meet at a
+// barrier after every tile, so that they read each tile together (a warp's
+// share is 512 B of every 4 KB row; warps spread over tiles lose DRAM row
+// locality: 0.66 against 0.89 of the copy peak on 10^9 normal points);
+// elsewhere (every point takes the edge test: bound by issue) they run
+// free and one warp's deferred points do not hold the others.
 constexpr int kCountRing = 256;
 
 // Block-wide sum to thread 0 (s_w: one slot per warp).
@@ -699,6 +707,7 @@ __global__ void __launch_bounds__(kFiltThreads, 5) filter_count_kernel(const flo
     const int64_t per = ceil_div(ntiles, (int64_t)gridDim.x);
     const int64_t t1 = min(ntiles, (int64_t)(blockIdx.x + 1) * per);
     uint32_t part = 0;   // this thread's share of the block total
+    bool first = true, lockstep = true;
     for (int64_t w0 = (int64_t)blockIdx.x * per; w0 < t1; w0 += kCountRing) {
         const int64_t w1 = min(t1, w0 + kCountRing);
         for (int64_t tile = w0; tile < w1; ++tile) {
@@ -715,8 +724,15 @@ __global__ void __launch_bounds__(kFiltThreads, 5) filter_count_kernel(const flo
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
             if (lane == 0 && c) atomicAdd(&s_cnt[tile - w0], c);
+            if (first) {   // the block's first tile decides (block-uniform: read after the barrier)
+                __syncthreads();
+                lockstep = s_cnt[tile - w0] < (uint32_t)(kFiltTile / 4);
+                first = false;
+            } else if (lockstep) {
+                __syncthreads();
+            }
         }
-        __syncthreads();
+        __syncthreads();   // every warp's counts of the window are in
         for (int64_t i = threadIdx.x; i < w1 - w0; i += kFiltThreads) {
             const uint32_t v = s_cnt[i];
             status[w0 + i] = v;
