@@ -963,8 +963,10 @@ def learned_record(dev, stream, n, steps, warmup, train_sets, seed):
         h_fan = out[: int(cnt.item())].clone()
         res = {}
 
+        bufs = prop.outputs(n, dev)   # (allocated outside the timed calls, as ch_hull's)
+
         def learned_hull():
-            res["h"] = prop.hull_on_device(d, ws, stream, sync=False)
+            res["h"] = prop.hull_on_device(d, ws, stream, sync=False, out=bufs)
 
         ms_l = timed(learned_hull)
         idx_l, cnt_l, k_l, _ = res["h"]

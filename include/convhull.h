@@ -195,7 +195,8 @@ ch_status ch_hull_octagon_kgon(const float *pts, int64_t n, const float *dirs, i
  * pi / 4 with zero offset takes the octagon's integer direction), then
  * ch_hull_octagon_kgon with that polygon (K = 8: ch_hull).  params: device,
  * the MLP's BF16 parameters (ch_mlp_forward).  dirs_out (device, 128
- * floats, may be NULL) and k_out (device, may be NULL) receive the choice.
+ * floats, may be NULL: the K directions as (cos, sin) pairs, zeros after
+ * them) and k_out (device, may be NULL) receive the choice.
  * The hull is ch_hull's whatever the MLP outputs. */
 ch_status ch_hull_learned(const float *pts, int64_t n, const void *params, float *dirs_out, int32_t *k_out,
                           uint32_t *hull_idx, uint32_t *hull_count, void *ws, size_t ws_bytes, void *stream);

@@ -186,12 +186,13 @@ namespace {
 // ch_hull's launches with an optional second polygon between the octagon's
 // count pass and the fan
 cudaError_t hull_pipeline(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count, void *ws,
-                          const Layout &L, const KgonStage *kg, cudaStream_t st, const void *learn_params = nullptr)
+                          const Layout &L, const KgonStage *kg, cudaStream_t st, const void *learn_params = nullptr,
+                          float *learn_dirs = nullptr, int32_t *learn_k = nullptr)
 {
     const int variant = filter_variant();
     cudaError_t e = launch_extremes(pts, n, ws, L, at<uint32_t>(ws, L.ext8), true,
                                     at<unsigned long long>(ws, L.ctrl), (int64_t)L.zero_words, st, variant == 0,
-                                    learn_params);
+                                    learn_params, learn_dirs, learn_k);
     if (e == cudaSuccess) e = launch_filter(pts, n, ws, L, nullptr, nullptr, nullptr, true, st, variant, true, true, kg);
     if (e == cudaSuccess) e = launch_small_hull(ws, L, hull_idx, hull_count, st);
     if (e == cudaSuccess) e = launch_sort(ws, L, st);
@@ -248,10 +249,8 @@ extern "C" ch_status ch_hull_learned(const float *pts, int64_t n, const void *pa
     // the proposal runs in one more block of the extremes sweep
     LearnScratch *ls = at<LearnScratch>(ws, L.learn);
     const KgonStage kg{ls->dirs, &ls->K, 0, nullptr};
-    cudaError_t e = hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st, params);
-    if (e == cudaSuccess && dirs_out) e = cudaMemcpyAsync(dirs_out, ls->dirs, sizeof(ls->dirs), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, &ls->K, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    return cuda_status(e);
+    // (the learned block writes the choice to dirs_out and k_out itself)
+    return cuda_status(hull_pipeline(pts, n, hull_idx, hull_count, ws, L, &kg, st, params, dirs_out, k_out));
 }
 
 extern "C" ch_status ch_hull_batched(const float *pts, const int64_t *offsets, int32_t num_sets, uint32_t *hull_idx,

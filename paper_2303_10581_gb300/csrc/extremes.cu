@@ -307,12 +307,13 @@ __global__ void __launch_bounds__(kExtThreads, 2) extremes_kernel(const float *_
                                                                   void *ws, Layout L, uint32_t *ext8_out,
                                                                   int build_polygon, unsigned long long *zero_ptr,
                                                                   int64_t zero_words, uint32_t cap,
-                                                                  const __nv_bfloat16 *learn)
+                                                                  const __nv_bfloat16 *learn, float *learn_dirs,
+                                                                  int32_t *learn_k)
 {
     static_assert(kExtThreads == mlp::LT, "the learned block has the sweep's block size");
     const uint32_t nsweep = gridDim.x - (learn ? 1u : 0u);   // blocks of the sweep
     if (learn && blockIdx.x == nsweep) {
-        mlp::learned_choice_block(pts, n, learn, at<LearnScratch>(ws, L.learn));
+        mlp::learned_choice_block(pts, n, learn, at<LearnScratch>(ws, L.learn), learn_dirs, learn_k);
         return;
     }
     ExtCtrl *ctrl = at<ExtCtrl>(ws, L.extctrl);
@@ -958,7 +959,8 @@ int extremes_per_sm()
 
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
-                            cudaStream_t st, bool spec, const void *learn_params)
+                            cudaStream_t st, bool spec, const void *learn_params, float *learn_dirs,
+                            int32_t *learn_k)
 {
     const __nv_bfloat16 *learn = static_cast<const __nv_bfloat16 *>(learn_params);
     const unsigned extra = learn ? 1u : 0u;
@@ -976,7 +978,8 @@ cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout 
             spec_sample_kernel<<<kSampleBlocks, kSampleThreads, 0, st>>>(pts, n, ws, L, (uint32_t)blocks,
                                                                          (uint32_t)cap);
             extremes_kernel<true><<<(unsigned)blocks + extra, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, 1, zero_ptr,
-                                                                                   zero_words, (uint32_t)cap, learn);
+                                                                                   zero_words, (uint32_t)cap, learn,
+                                                                                   learn_dirs, learn_k);
             note_kernels(CH_K_EXTREMES, 2);
             probe_after(CH_K_EXTREMES, st);
             return cudaGetLastError();
@@ -988,7 +991,8 @@ cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout 
     if (blocks < 1) blocks = 1;
     probe_before(CH_K_EXTREMES, st);
     extremes_kernel<false><<<(unsigned)blocks + extra, kExtThreads, 0, st>>>(pts, n, ws, L, ext8, build_polygon ? 1 : 0,
-                                                                             zero_ptr, zero_words, 0u, learn);
+                                                                             zero_ptr, zero_words, 0u, learn,
+                                                                             learn_dirs, learn_k);
     note_kernels(CH_K_EXTREMES, 1);
     probe_after(CH_K_EXTREMES, st);
     return cudaGetLastError();

@@ -25,7 +25,8 @@ void probe_after(int kid, cudaStream_t st);
 // inside the final one (Octagon::spec), the filter's passes test only them
 cudaError_t launch_extremes(const float *pts, int64_t n, void *ws, const Layout &L, uint32_t *ext8,
                             bool build_polygon, unsigned long long *zero_ptr, int64_t zero_words,
-                            cudaStream_t st, bool spec = false, const void *learn_params = nullptr);
+                            cudaStream_t st, bool spec = false, const void *learn_params = nullptr,
+                            float *learn_dirs = nullptr, int32_t *learn_k = nullptr);
 
 cudaError_t launch_octagon(const float *pts, int64_t n, const uint32_t *ext8, void *ws, const Layout &L,
                            unsigned long long *zero_ptr, int64_t zero_words, cudaStream_t st);

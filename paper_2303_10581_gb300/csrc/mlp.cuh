@@ -45,7 +45,8 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 __device__ __forceinline__ void learned_choice_block(const float *__restrict__ pts, int64_t n,
-                                                     const __nv_bfloat16 *__restrict__ P, LearnScratch *ls)
+                                                     const __nv_bfloat16 *__restrict__ P, LearnScratch *ls,
+                                                     float *dirs_out = nullptr, int32_t *k_out = nullptr)
 {
     __shared__ float s_red[4][LT / 32];
     __shared__ uint32_t s_cnt[kIn];
@@ -144,6 +145,9 @@ __device__ __forceinline__ void learned_choice_block(const float *__restrict__ p
     for (int i = 1; i < 4; ++i)
         if (s_o[i] > s_o[best]) best = i;   // a NaN logit never wins
     const int K = 8 << best;
+    // (the caller's copy: the K directions, zeros after them)
+    if (dirs_out)
+        for (int k = K + lane; k < kMaxDirs; k += 32) dirs_out[2 * k] = dirs_out[2 * k + 1] = 0.0f;
     for (int k = lane; k < K; k += 32) {
         float u = fminf(fmaxf(s_o[4 + k], -0.45f), 0.45f);
         if (!(u == u)) u = 0.0f;
@@ -159,8 +163,15 @@ __device__ __forceinline__ void learned_choice_block(const float *__restrict__ p
         }
         ls->dirs[2 * k] = cx;
         ls->dirs[2 * k + 1] = cy;
+        if (dirs_out) {
+            dirs_out[2 * k] = cx;
+            dirs_out[2 * k + 1] = cy;
+        }
     }
-    if (lane == 0) ls->K = K;
+    if (lane == 0) {
+        ls->K = K;
+        if (k_out) *k_out = K;
+    }
 }
 
 

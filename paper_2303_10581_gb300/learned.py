@@ -100,18 +100,23 @@ class Proposal:
         ch_hull_kgon(pts, d, idx, cnt, ws.buf, stream)
         return idx, cnt, K
 
-    def hull_on_device(self, pts, ws, stream=None, sync=True):
+    def outputs(self, n, device):
+        """Output buffers for hull_on_device: (hull_idx, hull_count, K,
+        directions)."""
+        import torch
+        return (torch.empty(max(n, 1), dtype=torch.int32, device=device),
+                torch.zeros(1, dtype=torch.int32, device=device),
+                torch.zeros(1, dtype=torch.int32, device=device),
+                torch.empty(128, dtype=torch.float32, device=device))
+
+    def hull_on_device(self, pts, ws, stream=None, sync=True, out=None):
         """ch_hull_learned: features, MLP, the choice of K and directions and
         the hull with that second polygon, all on the device (no host
-        synchronisation inside the call).  Returns (hull_idx, hull_count,
-        K, directions (64, 2)) -- K and directions read back when sync."""
-        import torch
+        synchronisation inside the call).  out: buffers from outputs() (else
+        new ones).  Returns (hull_idx, hull_count, K, directions (64, 2)) --
+        K and directions read back when sync."""
         from . import ch_hull_learned
-        n = pts.shape[0]
-        idx = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
-        cnt = torch.zeros(1, dtype=torch.int32, device=pts.device)
-        dirs = torch.empty(128, dtype=torch.float32, device=pts.device)
-        k = torch.zeros(1, dtype=torch.int32, device=pts.device)
+        idx, cnt, k, dirs = out if out is not None else self.outputs(pts.shape[0], pts.device)
         ch_hull_learned(pts, self.params, dirs, k, idx, cnt, ws.buf, stream)
         if not sync:
             return idx, cnt, k, dirs

@@ -95,5 +95,5 @@ def test_learned_end_to_end_on_the_device(kind):
         hidx, hcnt, K, dirs = prop.hull_on_device(d, ws)
         ws.check()
         assert K in (8, 16, 32, 64)
-        assert np.all(np.abs(dirs[:K]) <= 1.0)
+        assert np.all(np.abs(dirs[:K]) <= 1.0) and np.all(dirs[K:] == 0.0)
         assert np.array_equal(hidx[: int(hcnt.item())].cpu().numpy().view(np.uint32), oracle.convex_hull(p)[2])
