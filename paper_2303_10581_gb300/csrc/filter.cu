@@ -36,6 +36,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "fan.cuh"
 #include "launch.h"
 
 namespace ch {
@@ -681,9 +682,15 @@ __device__ __forceinline__ uint32_t block_sum_to0(uint32_t v, uint32_t (&s_w)[NW
     return t;
 }
 
+// fan_slots (the hull step, else NULL): on every fan_stride-th tile the
+// kept points' packed (far_key << 32 | ~index) go into the fan's bin slots
+// by atomicMax (read first: most points do not raise their bin), the
+// first level's farthest sampled point per bin without a pass of its own.
 template <int G, bool BOX>
-__global__ void __launch_bounds__(kFiltThreads, 5) filter_count_kernel(const float *__restrict__ pts, int64_t n,
-                                                                    void *ws, Layout L)
+__global__ void __launch_bounds__(kFiltThreads, BOX ? 4 : 5) filter_count_kernel(const float *__restrict__ pts, int64_t n,
+                                                                    void *ws, Layout L,
+                                                                    unsigned long long *fan_slots,
+                                                                    int32_t fan_stride)
 {
     __shared__ OctSmem so;
     __shared__ FiltQueue s_fq[NW];
@@ -720,6 +727,21 @@ __global__ void __launch_bounds__(kFiltThreads, 5) filter_count_kernel(const flo
             float px[kFiltItems], py[kFiltItems];
             const uint32_t keep = load_test<G, BOX>(pts, n, tile * kFiltTile, so, px, py, s_fq[threadIdx.x >> 5]);
             bits[tile * kFiltThreads + threadIdx.x] = (uint16_t)keep;
+            if (!BOX && fan_slots && tile % fan_stride == 0) {   // block-uniform (the hull step only)
+                // the kept points again from L2 (the tile was just read), so
+                // that the test's registers are free here
+                const float r2ref = far_ref(so);
+#pragma unroll 1
+                for (uint32_t m = keep; m; m &= m - 1u) {
+                    const int q = __ffs(m) - 1;
+                    const uint32_t i = (uint32_t)(tile * kFiltTile + ((q / G) * kFiltThreads + threadIdx.x) * G + q % G);
+                    const float2 p = __ldcg(reinterpret_cast<const float2 *>(pts) + i);
+                    const int b = fan_bin(__fsub_rn(p.x, so.cx), __fsub_rn(p.y, so.cy));
+                    const unsigned long long v =
+                        ((unsigned long long)far_key(p.x, p.y, so.cx, so.cy, r2ref) << 32) | (uint32_t)~i;
+                    if (v > __ldcg(fan_slots + b)) atomicMax(fan_slots + b, v);
+                }
+            }
             uint32_t c = __popc(keep);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -1121,7 +1143,10 @@ cudaError_t launch_two_pass(const float *pts, int64_t n, void *ws, const Layout 
     const int64_t ntiles = ceil_div(n, kFiltTile);
     const int64_t bc = std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>((int64_t)sm_count() * per_sm, kFiltMaxBlocks), ntiles));
-    filter_count_kernel<G, BOX><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L);
+    // the hull step's fan gathers its bin maxima in this pass
+    unsigned long long *fan_slots = (fan && !BOX) ? at<KgonCtrl>(ws, L.kgon_ctrl)->slot : nullptr;
+    filter_count_kernel<G, BOX><<<(unsigned)bc, kFiltThreads, 0, st>>>(pts, n, ws, L, fan_slots,
+                                                                       (int32_t)fan_sample_stride(ntiles));
     if (kg && (kg->kdev || kg->K != 8)) {   // the second polygon, over the octagon's survivors
         probe_after(CH_K_FILTER, st);
         const cudaError_t e = launch_kx_sv(pts, n, kg->dirs, kg->kdev, kg->K, kg->ext_out, ws, L, bc, st);

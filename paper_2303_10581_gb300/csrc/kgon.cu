@@ -9,9 +9,9 @@
 // centre of the bounding box, checked with exact signs to lie strictly
 // inside the octagon, hence strictly inside the hull.  The plane around c
 // is cut into kFanBins angular bins; the vertex of a bin is the input point
-// farthest from c among a sample (about kBinTiles evenly spaced 4096-point
-// tiles of the input),
-// and a bin the sample missed repeats the vertex before it.  For
+// farthest from c among a sample (the octagon survivors of about
+// kFanBinTiles evenly spaced 4096-point tiles of the input, fan.cuh), and a
+// bin the sample missed repeats the vertex before it.  For
 // consecutive vertices v, w every point strictly inside the triangle
 // (c, v, w) is a combination of c, v and w with positive weights, so it
 // lies strictly inside the hull and is no vertex of it: it is dropped.
@@ -23,11 +23,11 @@
 // per-tile counts and per-block totals) and its scatter pass, so the
 // scatter writes only the points that survive both tests:
 //
-//  fan_bins_kernel      octagon survivor count; per bin, the farthest sampled
-//                       input point (atomicMax of (far_key << 32 | ~index),
-//                       in shared memory per block, then in global memory)
-//  fan_build_kernel     exact centre check against the octagon; the vertex
-//                       of every bin
+//  (count pass)         per bin, the farthest sampled octagon survivor
+//                       (atomicMax of (far_key << 32 | ~index) into global
+//                       slots, on the sampled tiles, filter.cu)
+//  fan_build_kernel     octagon survivor count; exact centre check against
+//                       the octagon; the vertex of every bin
 //  fan_estimate_kernel  exact test of an input sample: whether the fan drops
 //                       at least an eighth of the octagon's survivors
 //  fan_refine_kernel    per tile of the filter: the kept points' exact fan
@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fan.cuh"
 #include "launch.h"
 
 namespace ch {
@@ -46,10 +47,8 @@ namespace {
 
 constexpr int FT = 512;                  // threads per block of the bins pass
 constexpr int FITEMS = 8;                // points per thread per tile there
-constexpr int FTILE = FT * FITEMS;       // 4096
 constexpr int CT = 1024;                 // threads per block of the refine pass: four
 constexpr int CG = CT / kFiltThreads;    // groups of kFiltThreads, each with its own tiles
-constexpr int64_t kBinTiles = 1536;      // the bins see every min(8, tiles / kBinTiles)-th tile (at least every tile)
 constexpr uint32_t kKgonMinS = 1u << 16; // fewer octagon survivors: not worth a pass
 constexpr int kFanSmem = kFanBins * 8;   // bins or vertices, 224 KB
 static_assert(kFiltItems == 16 && CT % kFiltThreads == 0, "refine pass: 16 keep bits per filter thread");
@@ -59,93 +58,6 @@ __device__ __forceinline__ float2 input_point(const float *pts, int64_t i)
     return __ldg(reinterpret_cast<const float2 *>(pts) + i);
 }
 
-// Bin of the direction (dx, dy): a pseudo-angle in [0, 4) that grows with
-// the angle counter-clockwise from +x, scaled to the bins.  Any value is
-// safe (it only picks a triangle); the conversion saturates and the result
-// is clamped.
-template <int NB = kFanBins>
-__device__ __forceinline__ int fan_bin(float dx, float dy)
-{
-    const float s = fabsf(dx) + fabsf(dy);
-    float a = 0.0f;
-    if (s > 0.0f) {
-        const float t = __fdividef(dy, s);
-        a = dx >= 0.0f ? (dy >= 0.0f ? t : 4.0f + t) : 2.0f - t;
-    }
-    // a is in [0, 4] (t in [-1, 1]; a NaN from an overflowed difference
-    // converts to 0): only the top needs a clamp
-    const int b = __float2int_rz(a * (NB / 4.0f));
-    return min(b, NB - 1);
-}
-
-template <int NB = kFanBins>
-__device__ __forceinline__ int next_bin(int b) { return b + 1 == NB ? 0 : b + 1; }
-template <int NB = kFanBins>
-__device__ __forceinline__ int prev_bin(int b) { return b == 0 ? NB - 1 : b - 1; }
-
-// a - b = s + e and a + b = s + e exactly (Knuth's two-sum, binary32
-// round to nearest; the intrinsics are never contracted into an FMA)
-__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e)
-{
-    s = __fsub_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
-}
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Order key for the farthest-point choice of a bin: |p - c|^2 - r2ref,
-// from the differences p - c and their squares as exact pairs (two-sum,
-// two-product by FMA), rounded once at the end.  The binary32 square
-// |p - c|^2 itself resolves only 2^-23 of its value, while on the unit
-// circle the radii of binary32 points differ by about 10^-7 and the top
-// points of a bin by far less: the vertex would be any of its top points
-// and the chords sag below the others.  Any key would keep the test exact
-// (a vertex only has to be an input point); this one finds the farthest.
-// r2ref: a squared distance of the set's scale (Sterbenz: the last
-// difference is exact when the sum is within a factor 2 of it).
-__device__ __forceinline__ uint32_t far_key(float px, float py, float cx, float cy, float r2ref)
-{
-    float dxh, dxl, dyh, dyl;
-    two_diff(px, cx, dxh, dxl);
-    two_diff(py, cy, dyh, dyl);
-    const float sxh = __fmul_rn(dxh, dxh), sxl = __fmaf_rn(dxh, dxh, -sxh);
-    const float syh = __fmul_rn(dyh, dyh), syl = __fmaf_rn(dyh, dyh, -syh);
-    float sh, sl;
-    two_sum(sxh, syh, sh, sl);
-    const float cross = __fmul_rn(2.0f, __fmaf_rn(dxh, dxl, __fmul_rn(dyh, dyl)));
-    const float lo = __fadd_rn(__fadd_rn(sl, __fadd_rn(sxl, syl)), cross);
-    return ord_key(__fadd_rn(__fsub_rn(sh, r2ref), lo));
-}
-
-// r2ref of far_key for a polygon's set: the squared distance from its
-// centre to its first vertex (binary32).
-__device__ __forceinline__ float far_ref(const Octagon &o)
-{
-    const float ux = __fsub_rn(o.ax[0], o.cx), uy = __fsub_rn(o.ay[0], o.cy);
-    return __fmaf_rn(ux, ux, __fmul_rn(uy, uy));
-}
-
-// Strictly inside a fan triangle (exact signs).  V: kFanBins vertices.
-// With o = orient(c, v, p) = +1 the triangle is (c, v, w), w the next
-// vertex, and p is inside iff orient(v, w, p) = orient(w, c, p) = +1; with
-// o = -1 it is (c, w, v), w the previous vertex, and p is inside iff
-// orient(w, v, p) = orient(c, w, p) = +1, i.e. orient(v, w, p) =
-// orient(w, c, p) = -1.
-//
-// fan_signs_f32 takes the three signs in binary32 (branch-free, so a
-// thread's items interleave): 1 inside, 0 outside, 2 undecided (a sign the
-// binary32 bound does not prove, and that matters); fan_inside_exact
-// settles the undecided ones.
-// The two signs with c as a vertex are taken with c as the reference point
-// (a cyclic shift of a triple keeps its orientation): orient(c, v, p) as
-// orient(v, p, c) and orient(w, c, p) as orient(p, w, c), so that both use
-// the differences p - c of the bin; orient_f32 certifies the sign of either
-// form with the same bound.
 // The signs orient_f32 certifies, as two flags (det > bound, -det > bound;
 // neither when undecided or when the terms may have overflowed): the same
 // arithmetic on the rounded differences a - c and b - c, without turning
@@ -207,70 +119,6 @@ __device__ __forceinline__ bool fan_live(const KgonCtrl *kc, const Octagon *oct,
     return s >= kKgonMinS && oct->has_edges && !oct->spec;   // spec: no keep bits to refine
 }
 
-// bc: the grid of the filter's count pass (its block totals are in
-// filt_bsum[0, bc)).
-__global__ void __launch_bounds__(FT) fan_bins_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L,
-                                                      int32_t bc)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *s_best = reinterpret_cast<unsigned long long *>(smem_raw);   // kFanBins
-    __shared__ uint32_t s_red[FT / 32];
-    const Octagon *oct = at<Octagon>(ws, L.oct);
-    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
-    if (oct->abort) return;   // the count pass left no totals
-    // octagon survivors: the sum of the count pass's block totals
-    const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    uint32_t t = 0;
-    for (int i = threadIdx.x; i < bc; i += FT) t += bsum[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) s_red[warp] = t;
-    __syncthreads();
-    uint32_t s = 0;
-    for (int w = 0; w < FT / 32; ++w) s += s_red[w];
-    if (blockIdx.x == 0 && threadIdx.x == 0) kc->s_oct = s;
-    if (s < kKgonMinS || !oct->has_edges || oct->spec) return;
-    for (int i = threadIdx.x; i < kFanBins; i += FT) s_best[i] = 0ull;
-    __syncthreads();
-    const float cx = oct->cx, cy = oct->cy, r2ref = far_ref(*oct);
-    const int64_t ntiles = ceil_div(n, FTILE);
-    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(8, ntiles / kBinTiles));   // every stride-th tile
-    const int64_t nsamp = ceil_div(ntiles, stride);
-    // two sample tiles per trip (k and k + grid: twice the loads in flight
-    // of one 512-thread block per SM); the next two stream into L2 meanwhile
-    const int64_t g = gridDim.x;
-    for (int64_t k = blockIdx.x; k < nsamp; k += 2 * g) {
-        if (threadIdx.x < 2 && k + (2 + threadIdx.x) * g < nsamp) {
-            const int64_t nb = (k + (2 + threadIdx.x) * g) * stride * FTILE;
-            const uint32_t nn = (uint32_t)std::min<int64_t>(FTILE, n - nb);
-            if (((reinterpret_cast<uintptr_t>(pts + 2 * nb)) & 15u) == 0) bulk_prefetch_l2(pts + 2 * nb, (nn * 8u) & ~15u);
-        }
-        float2 p[2 * FITEMS];
-#pragma unroll
-        for (int r = 0; r < 2 * FITEMS; ++r) {
-            const int64_t q = (k + (r / FITEMS) * g) * stride * FTILE + (r % FITEMS) * FT + threadIdx.x;
-            p[r] = q < n ? input_point(pts, q) : make_float2(0.0f, 0.0f);
-        }
-#pragma unroll
-        for (int r = 0; r < 2 * FITEMS; ++r) {
-            const int64_t q = (k + (r / FITEMS) * g) * stride * FTILE + (r % FITEMS) * FT + threadIdx.x;
-            if (q < n) {
-                const float dx = p[r].x - cx, dy = p[r].y - cy;
-                const int b = fan_bin(dx, dy);
-                const unsigned long long v =
-                    ((unsigned long long)far_key(p[r].x, p[r].y, cx, cy, r2ref) << 32) | (uint32_t)~(uint32_t)q;
-                if (v > s_best[b]) atomicMax(&s_best[b], v);   // the read only saves atomics
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kFanBins; i += FT) {
-        const unsigned long long v = s_best[i];
-        if (v != 0ull && v > __ldcg(&kc->slot[i])) atomicMax(&kc->slot[i], v);
-    }
-}
-
 // One thread per bin (kFanBins / BT blocks).  The vertex of bin b is the
 // sampled point of the last non-empty bin at or before b, cyclically: a
 // max-scan of "non-empty bin index" inside the block, and for the bins
@@ -291,17 +139,35 @@ __device__ __forceinline__ int block_max(int v, int *s_w)
     return m;
 }
 
-__global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L)
+// bc: the grid of the filter's count pass (its block totals are in
+// filt_bsum[0, bc)); the count pass gathered the bins' farthest sampled
+// points (filter.cu).
+__global__ void __launch_bounds__(BT) fan_build_kernel(const float *__restrict__ pts, int64_t n, void *ws, Layout L,
+                                                       int32_t bc)
 {
     __shared__ int s_w[BT / 32];
     __shared__ int s_scan[BT / 32];
     __shared__ int s_ok;
+    __shared__ uint32_t s_sum[BT / 32];
     const Octagon *oct = at<Octagon>(ws, L.oct);
-    const KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
+    KgonCtrl *kc = at<KgonCtrl>(ws, L.kgon_ctrl);
     Kgon *g = at<Kgon>(ws, L.kgon);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    uint32_t s;
-    if (!fan_live(kc, oct, s)) {
+    // octagon survivors: the sum of the count pass's block totals (none
+    // when the call was aborted: the count pass left no totals)
+    uint32_t s = 0;
+    if (!oct->abort) {
+        const uint32_t *bsum = at<uint32_t>(ws, L.filt_bsum);
+        uint32_t t = 0;
+        for (int i = (int)tid; i < bc; i += BT) t += bsum[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_sum[warp] = t;
+        __syncthreads();
+        for (int w = 0; w < BT / 32; ++w) s += s_sum[w];
+    }
+    if (blockIdx.x == 0 && tid == 0) kc->s_oct = s;   // read by the later fan kernels
+    if (!(s >= kKgonMinS && oct->has_edges && !oct->spec)) {   // (fan_live, before s_oct is visible)
         if (blockIdx.x == 0 && tid == 0) g->ok = 0u;
         return;
     }
@@ -625,7 +491,6 @@ cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blo
 {
     const int sms = sm_count();
     static const bool attrs = [] {
-        cudaFuncSetAttribute(fan_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
         cudaFuncSetAttribute(fan_refine_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
         cudaFuncSetAttribute(fan_refine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFanSmem);
         return true;
@@ -634,12 +499,11 @@ cudaError_t launch_fan(const float *pts, int64_t n, bool vec, int64_t filter_blo
     const int32_t bc = (int32_t)filter_blocks;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(sms, filter_blocks));
     probe_before(CH_K_KGON, st);
-    fan_bins_kernel<<<sms, FT, kFanSmem, st>>>(pts, n, ws, L, bc);
-    fan_build_kernel<<<kFanBins / BT, BT, 0, st>>>(pts, n, ws, L);
+    fan_build_kernel<<<kFanBins / BT, BT, 0, st>>>(pts, n, ws, L, bc);
     fan_estimate_kernel<<<sms, 256, 0, st>>>(pts, n, ws, L);
     if (vec) fan_refine_kernel<2><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
     else fan_refine_kernel<1><<<(unsigned)grid, CT, kFanSmem, st>>>(pts, n, ws, L, bc);
-    note_kernels(CH_K_KGON, 4);
+    note_kernels(CH_K_KGON, 3);
     probe_after(CH_K_KGON, st);
     return cudaGetLastError();
 }
