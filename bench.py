@@ -168,19 +168,23 @@ class ClockSampler:
 SMALL_HULL = 512   # at most this many points to sort: one block sorts and chains them (no sort passes)
 
 
-def algorithmic_bytes(kernel, n, s_list, t_list, f_list=None):
+def algorithmic_bytes(kernel, n, s_list, t_list, f_list=None, spec_list=None):
     """Bytes a kernel must move in one step (all its launches for the step's
     sets), from the data it reads and writes by definition; s_list holds the
     octagon-filter survivors of each set, t_list the points the hull step
     sorts (the survivors of the fan test as well, when it ran), f_list the
     points left by the fan's first level (t_list when absent: no second
-    level).  Sets with at most SMALL_HULL points to sort run no sort and
-    chain kernels."""
+    level), spec_list 1 for the sets the speculative sweep served (their
+    points were read by the extremes sweep: the filter only writes its
+    survivors; the candidates it re-reads are not counted).  Sets with at
+    most SMALL_HULL points to sort run no sort and chain kernels."""
     f_list = t_list if f_list is None else f_list
+    spec_list = [0] * len(s_list) if spec_list is None else spec_list
     if kernel == "extremes":
         return sum(8 * n for _ in s_list)                   # read the points
     if kernel == "filter":
-        return sum(8 * n + 12 * f for f in f_list)          # read points, write key + payload per point kept
+        # read points (unless the sweep served), write key + payload per point kept
+        return sum((0 if sp else 8 * n) + 12 * f for f, sp in zip(f_list, spec_list))
     if kernel == "kgon":
         # the fan test of the octagon survivors when it ran (read their
         # coordinates); otherwise only samples.  The second level reads the
@@ -227,6 +231,19 @@ def fan_rates(tr, dist):
     default."""
     rec = (tr.get("per_dist") or {}).get(dist) or tr
     return rec["warp_inst_per_survivor"], rec["dram_per_algorithmic_byte"]
+
+
+def traffic_per_launch(kernel, tr, n, s_list, t_list, f_list, spec_list, dists, steps, launches):
+    """DRAM bytes per launch of `kernel` from a traffic record: each set's
+    algorithmic bytes times the ratio captured for its distribution (the
+    record's default for the others)."""
+    total = 0.0
+    for k in range(len(s_list)):
+        one = lambda lst: [lst[k]] if lst is not None else None
+        b = algorithmic_bytes(kernel, n, [s_list[k]], [t_list[k]], one(f_list), one(spec_list))
+        rec = (tr.get("per_dist") or {}).get(dists[k]) or tr
+        total += rec["dram_per_algorithmic_byte"] * b
+    return int(total * steps / launches)
 
 
 def alu_roofline(dom_ms, dom_launches, steps, n, s_list, t_list, clk, dev, dists=None, f_list=None):
@@ -398,7 +415,7 @@ def run_ours(args):
     if dom_launches and dominant == "kgon":
         roof = alu_roofline(dom_ms, dom_launches, args.steps, n, surv, sorted_pts, clk, dev, list(DISTS), fan1)
     if dom_launches and roof is None:
-        per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts, fan1)
+        per_step_bytes = algorithmic_bytes(dominant, n, surv, sorted_pts, fan1, spec)
         if per_step_bytes is not None:
             # algorithmic bytes of all timed launches over their summed event
             # time (= per-launch bytes over the average launch duration)
@@ -408,7 +425,8 @@ def run_ours(args):
             tr = load_traffic(dominant)
             roof = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                    "traffic": int(tr["dram_per_algorithmic_byte"] * per_launch_bytes) if tr else None,
+                    "traffic": traffic_per_launch(dominant, tr, n, surv, sorted_pts, fan1, spec, list(DISTS),
+                                                  args.steps, dom_launches) if tr else None,
                     "traffic_source": tr["capture"] if tr else None,
                     "algorithmic_bytes_per_launch": int(per_launch_bytes), "avg_launch_ms": round(avg_ms, 4)}
 
@@ -416,7 +434,7 @@ def run_ours(args):
     filt = None
     if probe_all["filter"][1]:
         fms = probe_all["filter"][0]
-        fb = algorithmic_bytes("filter", n, surv, sorted_pts, fan1)
+        fb = algorithmic_bytes("filter", n, surv, sorted_pts, fan1, spec)
         filt = {"gpoints_s": round(pts_per_step / (fms * 1e-3) / 1e9, 2), "ms_per_set": round(fms / len(DISTS), 4),
                 "gbs": round(fb / (fms * 1e-3) / 1e9, 1), "frac_of_peak": round(fb / (fms * 1e-3) / 1e9 / peak, 4)}
 

@@ -38,6 +38,22 @@ def test_algorithmic_bytes_with_the_second_fan_level():
     assert bench.algorithmic_bytes("sort_pass", N, S, T2, F) == sum(4 * 24 * t for t in T2[1:])
 
 
+def test_filter_bytes_of_a_set_the_speculative_sweep_served():
+    # the normal set's points were read by the extremes sweep: its filter
+    # only writes the survivors
+    F = [69, 16_543_492, 118_191]
+    assert bench.algorithmic_bytes("filter", N, S, T, F, [1, 0, 0]) == 12 * 69 + sum(8 * N + 12 * f for f in F[1:])
+
+
+def test_traffic_per_launch_takes_each_distributions_ratio():
+    rec = {"dram_per_algorithmic_byte": 1.0,
+           "per_dist": {"circle": {"dram_per_algorithmic_byte": 1.2}, "displaced": {"dram_per_algorithmic_byte": 1.1}}}
+    F = [69, 16_543_492, 118_191]
+    got = bench.traffic_per_launch("filter", rec, N, S, T, F, [1, 0, 0], ["normal", "circle", "displaced"], 5, 10)
+    want = (1.0 * 12 * 69 + 1.2 * (8 * N + 12 * F[1]) + 1.1 * (8 * N + 12 * F[2])) * 5 / 10
+    assert got == int(want)
+
+
 @pytest.fixture
 def one_device(monkeypatch):
     class Props:
