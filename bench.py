@@ -61,6 +61,9 @@ def parse():
                          "kgon: K-direction filter polygons against the octagon")
     ap.add_argument("--sets", type=int, default=4096, help="sets of the batched workload")
     ap.add_argument("--train-sets", type=int, default=32, help="training sets per family (learned workload)")
+    ap.add_argument("--sequential-sets", action="store_true",
+                    help="run the step's sets one after another on one stream (default: one stream and workspace "
+                         "per set, the independent hulls overlapping)")
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload: skip the records of the 10^9-point filter, the batch and the learned proposal")
     ap.add_argument("--autotune", action="store_true",
@@ -346,15 +349,36 @@ def run_ours(args):
     n = args.n
     host = make_inputs(n, args.seed)
     d_pts = [torch.from_numpy(p).to(dev) for p in host]
-    ws = ch.Workspace(n, device=dev)
+    # one workspace per set: the step's hulls are independent problems and
+    # run on streams of their own (unless --sequential-sets), so that one
+    # set's latency-bound stages overlap another's streaming ones
+    wss = [ch.Workspace(n, device=dev) for _ in DISTS]
     ch.ch_filter_variant(args.filter_variant)
     hull_idx = [torch.empty(n, dtype=torch.int32, device=dev) for _ in DISTS]
     hull_cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in DISTS]
     stream = torch.cuda.current_stream()
+    set_streams = ([stream] * len(DISTS) if args.sequential_sets
+                   else [torch.cuda.Stream(device=dev) for _ in DISTS])
+
+    def sequential_step():
+        for k in range(len(DISTS)):
+            ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], wss[k].buf, stream)
 
     def step():
+        if args.sequential_sets:
+            sequential_step()
+            return
+        start = torch.cuda.Event()
+        start.record(stream)
+        done = []
         for k in range(len(DISTS)):
-            ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+            set_streams[k].wait_event(start)
+            ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], wss[k].buf, set_streams[k])
+            ev = torch.cuda.Event()
+            ev.record(set_streams[k])
+            done.append(ev)
+        for ev in done:
+            stream.wait_event(ev)
 
     def barrier():
         if world > 1:
@@ -364,29 +388,34 @@ def run_ours(args):
     # warm-up, then one probed step for the kernel shares and survivor counts
     for _ in range(args.warmup):
         step()
-    ws.check()
-    # one probed step, set by set: event time of every kernel
+    torch.cuda.synchronize()
+    for w in wss:
+        w.check()
+    # one probed step, set by set on one stream: event time of every kernel
     per_set = {}
     probe_all = {k: (0.0, 0) for k in KERNEL_IDS}
     surv, sorted_pts, spec, fan1 = [], [], [], []
     for k in range(len(DISTS)):
         ch.ch_probe_start(KERNEL_IDS, max_launches=64)
-        ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+        ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], wss[k].buf, stream)
         pr = ch.ch_probe_stop()
         per_set[DISTS[k]] = {kk: round(v[0], 4) for kk, v in pr.items() if v[1]}
         probe_all = {kk: (probe_all[kk][0] + pr[kk][0], probe_all[kk][1] + pr[kk][1]) for kk in KERNEL_IDS}
-        c = ch.ch_hull_counts(ws.buf, n, stream)
+        c = ch.ch_hull_counts(wss[k].buf, n, stream)
         surv.append(c[0])
         sorted_pts.append(c[1])
         spec.append(c[2])
         fan1.append(c[3])
-    ws.check()
+    for w in wss:
+        w.check()
     dominant = max(probe_all, key=lambda k: probe_all[k][0])
     total_probe = sum(v[0] for v in probe_all.values())
     shares = {k: round(v[0] / total_probe, 4) for k, v in probe_all.items() if v[1]}
     hull_sizes = [int(c.item()) for c in hull_cnt]
 
-    # timed region: the dominant kernel's launches are event-timed on the stream
+    # timed region: the dominant kernel's launches are event-timed on the
+    # streams they are launched on (with the sets overlapping, these times
+    # include the other sets' share of the GPU)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -401,14 +430,27 @@ def run_ours(args):
     barrier()
     probe = ch.ch_probe_stop()
     clk = clocks.stop()
-    ws.check()
+    for w in wss:
+        w.check()
     ms = t0.elapsed_time(t1) / args.steps
     ms_max = max_over_ranks(ms, dev)
     pts_per_step = len(DISTS) * n
     value = job_rate(world, pts_per_step, ms_max)
     launches_per_step = sum(v[1] for v in probe.values()) / args.steps
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: its launch times from a second timed
+    # region of K steps with the sets one after another (with the sets
+    # overlapping, a launch's event time includes the other sets' share of
+    # the GPU); the same K steps, the same events on the launching stream
+    if not args.sequential_sets:
+        barrier()
+        ch.ch_probe_start([dominant], max_launches=64 * args.steps)
+        for _ in range(args.steps):
+            sequential_step()
+        barrier()
+        probe = ch.ch_probe_stop()
+        for w in wss:
+            w.check()
     dom_ms, dom_launches = probe[dominant]
     peak, peak_kind = peaks()
     roof = None
@@ -469,7 +511,7 @@ def run_ours(args):
             for k, evs in zip(order, ready):
                 for ev in evs:
                     stream.wait_event(ev)
-                ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], ws.buf, stream)
+                ch.ch_hull(d_pts[k], hull_idx[k], hull_cnt[k], wss[k].buf, stream)
                 cnt_host[k].copy_(hull_cnt[k], non_blocking=True)
             stream.synchronize()
             for k in range(len(DISTS)):
@@ -512,6 +554,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+exact", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_per_set": n, "sets_per_step": len(DISTS),
+                       "sets_schedule": ("one after another, one stream" if args.sequential_sets
+                                         else "one stream and workspace per set, overlapping"),
+                       "roofline_timing": ("the timed region" if args.sequential_sets else
+                                           "a second timed region of the same steps, sets one after another"),
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (2.4 GB)",
                        "survivors": dict(zip(DISTS, surv)), "sorted": dict(zip(DISTS, sorted_pts)),
                        "speculative_sweep": dict(zip(DISTS, spec)),
