@@ -122,7 +122,13 @@ ch_status ch_extremes_filter(const float *pts, int64_t n, uint32_t *ext8, uint32
  * lexicographically smallest (x, y) vertex; equal points count once (the
  * lowest index is reported); points on a hull edge are not vertices.
  * *hull_count (device) receives the vertex count: 0 for n == 0, 1 when all
- * points coincide, 2 when all are collinear. */
+ * points coincide, 2 when all are collinear.  Before the sort the hull step
+ * throws survivors away again (not in the paper; the hull is the same): a
+ * fan of triangles around the bounding-box centre whose vertices are the
+ * farthest sampled survivors of angular bins, and, when that leaves at least
+ * 2^19 points (CH_TUNE_FAN2_MIN_LOG2), a second fan over those with eight
+ * times as many bins; a survivor strictly inside a triangle (exact signs) is
+ * no hull vertex. */
 ch_status ch_hull(const float *pts, int64_t n, uint32_t *hull_idx, uint32_t *hull_count,
                   void *ws, size_t ws_bytes, void *stream);
 
@@ -303,7 +309,8 @@ typedef enum {
     CH_K_EMIT = 6,       /* compaction of the chain ranges                      */
     CH_K_FINISH = 7,     /* hull assembly                                       */
     CH_K_KGON = 8,       /* hull step: fan test of the octagon survivors
-                            (runs between FILTER's count and scatter passes) */
+                            (runs between FILTER's count and scatter passes;
+                            its second level after the scatter) */
     CH_K_COUNT = 9
 } ch_kernel_id;
 
@@ -311,11 +318,13 @@ typedef enum {
  * is set in kernel_mask is bracketed by two CUDA events recorded on its
  * launch stream, for at most max_launches groups per id.  A group is the
  * kernels one step launches back to back under that id: one for
- * EXTREMES, OCTAGON, SORT_HIST, SORT_PASS (one per pass), EMIT, FINISH;
- * two for FILTER with the two-pass schedule (count, scatter; in ch_hull
- * each is its own group, KGON runs between them), one with the single pass;
- * two for CHAIN (chains, tree merge); four for KGON (bins, fan vertices,
- * estimate, refine of the keep decisions).  Kernel-launch
+ * EXTREMES, OCTAGON, SORT_HIST, SORT_PASS (one per pass), FINISH; two for
+ * EMIT (offsets, copy); two for FILTER with the two-pass schedule (count,
+ * scatter; in ch_hull each is its own group, KGON runs between them), one
+ * with the single pass; two for CHAIN (chains, tree merge); for KGON three
+ * (fan vertices, estimate, refine of the keep decisions; the count pass
+ * gathers the bins) and four for its second level (sub-bin maxima,
+ * vertices, test, compaction).  Kernel-launch
  * counting for all ids restarts at zero.  Host-only bookkeeping; creates
  * the events.  Process-wide: one probe at a time, driven from one host
  * thread (see "Host threads" above). */
