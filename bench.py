@@ -352,7 +352,8 @@ def run_ours(args):
     # one workspace per set: the step's hulls are independent problems and
     # run on streams of their own (unless --sequential-sets), so that one
     # set's latency-bound stages overlap another's streaming ones
-    wss = [ch.Workspace(n, device=dev) for _ in DISTS]
+    wss = ([ch.Workspace(n, device=dev)] * len(DISTS) if args.sequential_sets
+           else [ch.Workspace(n, device=dev) for _ in DISTS])
     ch.ch_filter_variant(args.filter_variant)
     hull_idx = [torch.empty(n, dtype=torch.int32, device=dev) for _ in DISTS]
     hull_cnt = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in DISTS]
